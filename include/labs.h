@@ -1,0 +1,202 @@
+/*
+ * labs.h -- C ABI of the GB300 (sm_103a) memetic tabu search (MTS) solver for
+ * Low Autocorrelation Binary Sequences (LABS), after arXiv 2504.00987.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Sequence format.  A length-N sequence S = s_1 .. s_N, s_i in {-1, +1}
+ *   (Sec. II), is packed LSB-first into W = ceil(N/64) uint64 words: s_{i+1}
+ *   is bit (i % 64) of word (i / 64), bit 1 <-> +1.  Bits at positions >= N
+ *   are ignored by every call (read as zero) and written as zero.
+ *   A batch of B sequences is B * W contiguous words (row-major, 8-byte
+ *   aligned).  3 <= N <= LABS_MAX_N.
+ * Energy (Eq. 1, Eq. 2): C_k = sum_{i=1}^{N-k} s_i s_{i+k}, E = sum_k C_k^2,
+ *   exact in int32.  Merit factor (Eq. 3): F = N^2 / (2 E).
+ * Memory.  The caller owns every buffer.  "d_" pointers are device memory
+ *   (cudaMalloc, cudaMallocAsync or a framework's allocator); "h_" pointers
+ *   are host memory.  A pointer of the wrong kind is rejected with
+ *   LABS_EINVAL before any launch.
+ * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   Calls are asynchronous on that stream unless documented as blocking.
+ * Errors.  Every entry point returns a LABS_* status.  A non-OK status
+ *   leaves a message for labs_last_error() (thread-local).  The library
+ *   never aborts, never exits and prints nothing.
+ * Randomness.  Every random decision is one 32-bit word of Philox4x32-10
+ *   (Salmon et al., SC'11) under key (seed low 32 bits, seed high 32 bits)
+ *   at counter (instance, a, b, purpose); see labs_params for the draws.
+ *   Results are a pure function of (parameters, seed, instance): the same
+ *   instance gives the same trajectory alone, in a batch or after resume.
+ */
+#ifndef LABS_H
+#define LABS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LABS_OK 0
+#define LABS_EINVAL 1       /* bad argument (size, pointer kind, alignment, tail bits) */
+#define LABS_ENOMEM 2       /* a device or host allocation failed */
+#define LABS_ECUDA 3        /* a CUDA runtime call failed; see labs_last_error() */
+#define LABS_ETIMEOUT 4     /* a bounded device wait ran out */
+#define LABS_EBUSY 5        /* no free slot or queue entry */
+#define LABS_ENOTREADY 6    /* result not available yet */
+#define LABS_ECANCELED 7    /* request was cancelled */
+#define LABS_ENOTFOUND 8    /* unknown ticket */
+
+#define LABS_MAX_N 256
+#define LABS_MAX_W 4
+#define LABS_MAX_K 1024
+
+/* Replacement rule of the population loop. */
+#define LABS_REPLACE_RANDOM 0 /* Algorithm 1: a uniformly drawn member (default) */
+#define LABS_REPLACE_WORST 1  /* variant: the highest-E member, lowest index on ties */
+
+/* Why a replica stopped. */
+#define LABS_RUN_BUDGET 0  /* generation or step budget used up */
+#define LABS_RUN_REACHED 1 /* E(best) <= target_E */
+#define LABS_RUN_STOPPED 2 /* another replica of the same run reached target_E (GLF) */
+
+typedef void* labs_stream_t; /* a cudaStream_t */
+
+/*
+ * Parameters of Memetic-Tabu (Algorithm 1 / Algorithm 3 of the paper).
+ *
+ * Draws per replica (instance i), generation g, as Philox words (x, y, z, w):
+ *   population member p, word w .. (i, p, w, 1): x = low half, y = high half
+ *   (i, g, 0, 2) ...................... x coin, y/z/w tournament entrants a, b, c
+ *   (i, g, 1, 2) ...................... x entrant d, y crossover cut, z sampled
+ *                                       member, w tabu length
+ *   (i, g, 2, 2) ...................... x replaced member
+ *   (i, g, j/4, 3) .................... word j%4: mutation draw of bit j
+ *   (i, g, t, 4) ...................... x tie pick, y tenure of tabu step t
+ * randInt(a, b) = a + floor(u * (b - a + 1) / 2^32).
+ * The generation step: with probability p_comb two binary tournaments
+ * (lower E wins, lower index on ties) pick P1, P2 and the child is
+ * P1 bits [0, c) | P2 bits [c, N), c = randInt(1, N-1); otherwise the child
+ * is a copy of member randInt(0, K-1).  Every bit of the child then flips
+ * iff its draw < p_mut_u32.  The tabu search (Algorithm 2) runs for
+ * maxIter = floor(N/2) + randInt(0, N) steps (or `max_iter`), with tenure
+ * randInt(floor(maxIter/10), floor(12 maxIter/100)); a bit is admissible iff
+ * its tabu has expired or flipping it beats the search's best (aspiration);
+ * ties for the admissible minimum are broken by the tie draw in ascending
+ * bit order.  The child replaces a member (replace_policy) and the replica's
+ * best on a strictly lower energy.
+ */
+typedef struct labs_params {
+    int32_t N;               /* 3 .. LABS_MAX_N */
+    int32_t K;               /* population size, 1 .. LABS_MAX_K (paper: 100) */
+    uint32_t p_comb_u32;     /* crossover iff coin < p_comb_u32; 0.9 -> 3865470566 */
+    uint32_t p_mut_u32;      /* per-bit flip iff draw < p_mut_u32; 0 -> floor(2^32/N) */
+    int32_t replace_policy;  /* LABS_REPLACE_* */
+    int32_t target_E;        /* stop a replica once E(best) <= target_E; -1: no target */
+    int64_t max_generations; /* per replica; -1: unlimited */
+    int64_t max_steps;       /* tabu steps per replica; -1: unlimited.  A budget can end a
+                                tabu search early; that generation still completes. */
+    int32_t max_iter;        /* tabu length; -1: floor(N/2) + randInt(0, N) */
+    int32_t glf;             /* nonzero: a replica reaching target_E stops every replica of
+                                the run at its next generation boundary (Algorithm 3 GLF) */
+    int32_t* d_trace;        /* nullable, device: per replica trace_cap records {g, t, j, E}
+                                (t >= 1: tabu step; t == 0: end of generation g with
+                                j = replaced member, E = E(child)) */
+    int64_t trace_cap;       /* records per replica in d_trace */
+} labs_params;
+
+/* Per-replica result in device memory (64 bytes). */
+typedef struct labs_device_result {
+    uint64_t seq[LABS_MAX_W]; /* best sequence of the replica */
+    int32_t E;                /* its energy */
+    int32_t status;           /* LABS_RUN_* */
+    int64_t generations;      /* completed generations */
+    int64_t steps;            /* tabu steps taken (flip evaluations = steps * N) */
+    int64_t trace_len;        /* records written to the replica's trace */
+} labs_device_result;
+
+/* Per-replica result in host memory. */
+typedef struct labs_result {
+    uint64_t seq[LABS_MAX_W];
+    int32_t E;
+    int32_t N;
+    double F;                 /* merit factor N^2 / (2E), Eq. 3 */
+    int64_t generations;
+    int64_t steps;
+    int64_t flip_evals;       /* steps * N */
+    int64_t trace_len;
+    uint64_t instance;
+    double seconds;           /* wall time of the whole call */
+    int32_t status;
+    int32_t pad;
+} labs_result;
+
+/* Options of a standalone tabu search batch. */
+typedef struct labs_tabu_opts {
+    int32_t max_iter;        /* steps; -1: floor(N/2) + randInt(0, N) from draw (i, g, 1, 2).w */
+    uint32_t generation;     /* g of the draws (a search inside MTS uses its generation) */
+    uint64_t first_instance; /* sequence b uses instance first_instance + b */
+    int64_t trace_cap;       /* records {g, t, j, E} per sequence in d_trace */
+} labs_tabu_opts;
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* labs_last_error(void);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int32_t labs_version(void);
+
+/*
+ * labs_energy_batch -- Eq. 1 and Eq. 2 for B sequences.
+ *   d_seqs  device, B * W uint64, packed sequences (read only).
+ *   N       3 .. LABS_MAX_N.   B >= 0 (B == 0 is a no-op).
+ *   d_E     device, B int32: E of each sequence.
+ *   d_C     device, nullable, B * (N-1) int32: C_1 .. C_{N-1} of each sequence.
+ * Asynchronous on `stream`.
+ */
+int32_t labs_energy_batch(const uint64_t* d_seqs, int32_t N, int64_t B, int32_t* d_E,
+                          int32_t* d_C, labs_stream_t stream);
+
+/*
+ * labs_tabu_run -- B independent tabu searches (Algorithm 2 / Algorithm 4),
+ * one from each start sequence, each scoring all N one-bit-flip neighbours
+ * per step with incremental correlations (Sec. III.C).
+ *   d_start  device, B * W uint64 start sequences.
+ *   seed     Philox key; sequence b uses instance opts->first_instance + b
+ *            and generation opts->generation.
+ *   d_best   device, B * W uint64: best sequence visited (bestSeqTS).
+ *   d_bestE  device, B int32: its energy.
+ *   d_steps  device, nullable, B int64: steps taken.
+ *   d_trace  device, nullable, B * trace_cap * 4 int32 records {g, t, j, E}.
+ * Asynchronous on `stream`.
+ */
+int32_t labs_tabu_run(const uint64_t* d_start, int32_t N, int64_t B, uint64_t seed,
+                      const labs_tabu_opts* opts, uint64_t* d_best, int32_t* d_bestE,
+                      int64_t* d_steps, int32_t* d_trace, labs_stream_t stream);
+
+/*
+ * labs_mts_launch -- `replicas` independent Memetic-Tabu replicas (Algorithm
+ * 3: one population per replica, all on the device), instances
+ * first_instance .. first_instance + replicas - 1.  Asynchronous.
+ *   d_out   device, replicas labs_device_result.
+ *   d_glf   device, nullable, one uint32 global termination flag shared by
+ *           the replicas of this launch; the caller zeroes it.  Required
+ *           when P->glf is nonzero.
+ * Fails with LABS_EINVAL if no target, generation or step budget bounds the
+ * run.
+ */
+int32_t labs_mts_launch(const labs_params* P, uint64_t seed, uint64_t first_instance,
+                        int64_t replicas, labs_device_result* d_out, uint32_t* d_glf,
+                        labs_stream_t stream);
+
+/*
+ * labs_mts_run -- labs_mts_launch plus the device scratch it needs (results,
+ * GLF), the copy of the results to h_out[replicas] and the merit factors.
+ * BLOCKING: returns once the results are in host memory.  Allocates and
+ * frees its scratch with cudaMallocAsync/cudaFreeAsync on `stream`.
+ */
+int32_t labs_mts_run(const labs_params* P, uint64_t seed, uint64_t first_instance,
+                     int64_t replicas, labs_result* h_out, labs_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LABS_H */

@@ -1,0 +1,131 @@
+"""torch-facing wrappers of the C ABI (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _native as nat
+
+P_COMB_U32 = 3865470566  # floor(0.9 * 2^32): p_comb = 0.9 (Sec. III.A)
+
+
+def p_mut_u32(N: int) -> int:
+    """floor(2^32 / N): per-bit mutation threshold for p_mutate = 1/N (Sec. III.A)."""
+    return (1 << 32) // N
+
+
+def words_for(N: int) -> int:
+    return (N + 63) // 64
+
+
+def version() -> int:
+    return int(nat.load().labs_version())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p | None:
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check_seqs(seqs: torch.Tensor, N: int) -> torch.Tensor:
+    if not seqs.is_cuda:
+        raise ValueError("sequences must be a CUDA tensor")
+    if seqs.dtype not in (torch.int64, torch.uint64):
+        raise ValueError("sequences must be int64/uint64 words")
+    if seqs.dim() != 2 or seqs.shape[1] != words_for(N):
+        raise ValueError(f"sequences must have shape (B, {words_for(N)})")
+    return seqs.contiguous()
+
+
+def energy_batch(seqs: torch.Tensor, N: int, with_C: bool = False, stream=None):
+    """E (Eq. 2) of each packed sequence, and optionally C_1..C_{N-1} (Eq. 1)."""
+    seqs = _check_seqs(seqs, N)
+    B = seqs.shape[0]
+    E = torch.empty(B, dtype=torch.int32, device=seqs.device)
+    C = torch.empty((B, max(N - 1, 1)), dtype=torch.int32, device=seqs.device) if with_C else None
+    nat.check(nat.load().labs_energy_batch(_ptr(seqs), N, B, _ptr(E), _ptr(C), _stream(stream)))
+    return (E, C) if with_C else E
+
+
+def tabu_run(start: torch.Tensor, N: int, seed: int, *, max_iter: int = -1, generation: int = 0,
+             first_instance: int = 0, trace_cap: int = 0, stream=None) -> dict:
+    """B independent tabu searches (Algorithm 2), one from each start sequence."""
+    start = _check_seqs(start, N)
+    B, dev = start.shape[0], start.device
+    best = torch.empty_like(start)
+    bestE = torch.empty(B, dtype=torch.int32, device=dev)
+    steps = torch.empty(B, dtype=torch.int64, device=dev)
+    trace = torch.zeros((B, trace_cap, 4), dtype=torch.int32, device=dev) if trace_cap > 0 else None
+    opts = nat.TabuOpts(max_iter, generation, first_instance, trace_cap)
+    nat.check(nat.load().labs_tabu_run(_ptr(start), N, B, seed, ctypes.byref(opts), _ptr(best),
+                                       _ptr(bestE), _ptr(steps), _ptr(trace), _stream(stream)))
+    return {"best": best, "bestE": bestE, "steps": steps, "trace": trace}
+
+
+def make_params(N: int, K: int = 100, *, p_comb_u32: int = P_COMB_U32, p_mut: int = 0,
+                replace_policy: int = nat.REPLACE_RANDOM, target_E: int = -1,
+                max_generations: int = -1, max_steps: int = -1, max_iter: int = -1,
+                glf: bool = False, trace: torch.Tensor | None = None) -> nat.Params:
+    """labs_params; `trace` is an int32 CUDA tensor of shape (replicas, cap, 4) or None."""
+    cap = 0 if trace is None else int(trace.shape[1])
+    ptr = None if trace is None else trace.data_ptr()
+    return nat.Params(N, K, p_comb_u32, p_mut, replace_policy, target_E, max_generations,
+                      max_steps, max_iter, 1 if glf else 0, ptr, cap)
+
+
+def mts_launch(params: nat.Params, seed: int, first_instance: int, replicas: int,
+               out: torch.Tensor | None = None, glf_flag: torch.Tensor | None = None,
+               device=None, stream=None) -> torch.Tensor:
+    """Asynchronous launch of `replicas` MTS replicas.  Returns the (replicas, 8) int64
+    device tensor holding one labs_device_result per replica (decode with
+    decode_results)."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        out = torch.empty((replicas, 8), dtype=torch.int64, device=dev)
+    if params.glf and glf_flag is None:
+        glf_flag = torch.zeros(1, dtype=torch.int32, device=out.device)
+    nat.check(nat.load().labs_mts_launch(ctypes.byref(params), seed, first_instance, replicas,
+                                         _ptr(out), _ptr(glf_flag), _stream(stream)))
+    return out
+
+
+def decode_results(out: torch.Tensor, N: int, first_instance: int = 0) -> list[dict]:
+    """labs_device_result rows (from mts_launch) -> dicts, on the host."""
+    h = out.detach().cpu()
+    rows = []
+    W = words_for(N)
+    for r in range(h.shape[0]):
+        row = h[r].tolist()
+        packed = row[4] & 0xFFFFFFFFFFFFFFFF
+        E = packed & 0xFFFFFFFF
+        status = (packed >> 32) & 0xFFFFFFFF
+        rows.append({
+            "instance": first_instance + r,
+            "seq": [w & 0xFFFFFFFFFFFFFFFF for w in row[:W]],
+            "E": E,
+            "F": N * N / (2.0 * E) if E > 0 else 0.0,
+            "status": status,
+            "generations": row[5],
+            "steps": row[6],
+            "flip_evals": row[6] * N,
+            "trace_len": row[7],
+        })
+    return rows
+
+
+def mts_run(params: nat.Params, seed: int, first_instance: int, replicas: int, stream=None) -> list[dict]:
+    """Blocking run of `replicas` MTS replicas; results in host memory."""
+    res = (nat.Result * max(replicas, 1))()
+    nat.check(nat.load().labs_mts_run(ctypes.byref(params), seed, first_instance, replicas, res,
+                                      _stream(stream)))
+    W = words_for(params.N)
+    return [{
+        "instance": int(r.instance), "seq": list(r.seq)[:W], "E": int(r.E), "F": float(r.F),
+        "status": int(r.status), "generations": int(r.generations), "steps": int(r.steps),
+        "flip_evals": int(r.flip_evals), "trace_len": int(r.trace_len), "seconds": float(r.seconds),
+    } for r in list(res)[:replicas]]

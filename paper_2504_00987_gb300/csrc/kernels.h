@@ -1,0 +1,50 @@
+// kernels.h -- launch interface between the C ABI (capi.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "labs.h"
+
+namespace lgpu {
+
+constexpr int kWarpsPerBlock = 4;
+
+struct MtsArgs {
+    int32_t N, K;
+    uint32_t p_comb_u32, p_mut_u32;
+    int32_t replace_policy, target_E;
+    int64_t max_generations, max_steps;
+    int32_t max_iter;
+    uint64_t seed, first_instance;
+    int64_t replicas;
+    labs_device_result* d_out;
+    uint32_t* d_glf;  // nullptr: no global termination flag
+    int4* d_trace;    // nullptr: no trace
+    int64_t trace_cap;
+    size_t smem_per_warp;
+};
+
+struct TabuArgs {
+    const uint64_t* d_start;
+    int32_t N;
+    int64_t B;
+    uint64_t seed, first_instance;
+    uint32_t generation;
+    int32_t max_iter;
+    uint64_t* d_best;
+    int32_t* d_bestE;
+    int64_t* d_steps;
+    int4* d_trace;
+    int64_t trace_cap;
+};
+
+size_t mts_smem_per_warp(int N, int K);
+cudaError_t launch_mts(const MtsArgs& a, cudaStream_t stream);
+cudaError_t launch_tabu(const TabuArgs& a, cudaStream_t stream);
+cudaError_t launch_energy(const uint64_t* d_seqs, int N, int64_t B, int32_t* d_E, int32_t* d_C,
+                          cudaStream_t stream);
+
+}  // namespace lgpu

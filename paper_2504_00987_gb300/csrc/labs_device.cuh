@@ -1,0 +1,118 @@
+// labs_device.cuh -- device primitives of the LABS solver (sm_103a).
+//
+// Sequences live in registers as NW = 2W 32-bit words, bit i of the vector
+// (word i / 32, bit i % 32) holding spin s_{i+1} (1 <-> +1).  A warp owns one
+// sequence; every lane keeps an identical copy of the words ("warp-uniform")
+// and lane l owns the indices l + 32q, q = 0 .. NW-1, of the per-index
+// arrays (correlations C_k, tabu expiry of bit j).
+#pragma once
+
+#include <cstdint>
+
+#include "labs.h"
+
+namespace lgpu {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+// Philox counter word 3 (purpose) of the RNG contract in labs.h.
+constexpr uint32_t kPurposeInit = 1u;
+constexpr uint32_t kPurposeGen = 2u;
+constexpr uint32_t kPurposeMut = 3u;
+constexpr uint32_t kPurposeStep = 4u;
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplications by fixed odd constants with a Weyl-sequence key
+// schedule; round r uses key + r * (golden-ratio, sqrt(3)-1) constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * x.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, x.x);
+        const uint32_t lo1 = 0xCD9E8D57u * x.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, x.z);
+        x = make_uint4(hi1 ^ x.y ^ k.x, lo1, hi0 ^ x.w ^ k.y, lo0);
+    }
+    return x;
+}
+
+__device__ __forceinline__ uint2 philox_key(uint64_t seed) {
+    return make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+}
+
+__device__ __forceinline__ uint4 draw4(uint2 key, uint32_t instance, uint32_t a, uint32_t b,
+                                       uint32_t purpose) {
+    return philox4x32_10(make_uint4(instance, a, b, purpose), key);
+}
+
+// randInt(lo, hi) inclusive: lo + floor(u * (hi - lo + 1) / 2^32).
+__device__ __forceinline__ int32_t rand_int(int32_t lo, int32_t hi, uint32_t u) {
+    const uint64_t span = static_cast<uint64_t>(static_cast<int64_t>(hi) - lo + 1);
+    return lo + static_cast<int32_t>((static_cast<uint64_t>(u) * span) >> 32);
+}
+
+// Bits [0, n) of 32-bit word v (n may lie outside the word).
+__device__ __forceinline__ uint32_t word_lowmask(int v, int n) {
+    const int hi = n - 32 * v;
+    return hi >= 32 ? kFull : (hi <= 0 ? 0u : ((1u << hi) - 1u));
+}
+
+// Position of the (n+1)-th set bit of x (n < popc(x)), by halving.
+__device__ __forceinline__ int nth_set_bit(uint32_t x, int n) {
+    int pos = 0;
+#pragma unroll
+    for (int width = 16; width >= 1; width >>= 1) {
+        const uint32_t lowbits = x & ((1u << width) - 1u);
+        const int c = __popc(lowbits);
+        if (n >= c) {
+            n -= c;
+            x >>= width;
+            pos += width;
+        } else {
+            x = lowbits;
+        }
+    }
+    return pos;
+}
+
+// out = in >> s for an NW-word vector and a warp-uniform runtime shift
+// 0 <= s < 32*NW: word moves by a log-depth select network, then one funnel
+// shift per word.  No dynamic register indexing.
+template <int NW>
+__device__ __forceinline__ void shr_uniform(const uint32_t (&in)[NW], int s, uint32_t (&out)[NW]) {
+    uint32_t a[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) a[w] = in[w];
+    const int ws = s >> 5;
+#pragma unroll
+    for (int step = 1; step < NW; step <<= 1) {
+        const bool take = (ws & step) != 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) a[w] = take ? (w + step < NW ? a[w + step] : 0u) : a[w];
+    }
+    const int bs = s & 31;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) out[w] = __funnelshift_r(a[w], w + 1 < NW ? a[w + 1] : 0u, bs);
+}
+
+// Flip bit i (warp-uniform) of an NW-word vector.
+template <int NW>
+__device__ __forceinline__ void flip_bit(uint32_t (&v)[NW], int i) {
+    const int wi = i >> 5;
+    const uint32_t m = 1u << (i & 31);
+#pragma unroll
+    for (int w = 0; w < NW; ++w) v[w] ^= (w == wi) ? m : 0u;
+}
+
+// Full-width reversal: bit (32*NW - 1 - i) of out = bit i of in.
+template <int NW>
+__device__ __forceinline__ void reverse_bits(const uint32_t (&in)[NW], uint32_t (&out)[NW]) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) out[w] = __brev(in[NW - 1 - w]);
+}
+
+}  // namespace lgpu

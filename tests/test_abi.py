@@ -1,0 +1,92 @@
+"""The C ABI library builds, loads without a GPU and exports every function
+include/labs.h declares; struct layouts of the binding match the header."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if hdr.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", hdr)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^[A-Za-z_][\w\s\*]*?\b(labs_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2504_00987_gb300 import _build, _native
+
+    _build.build()
+    return _native.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["labs_energy_batch", "labs_tabu_run", "labs_mts_launch", "labs_mts_run",
+                     "labs_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2504_00987_gb300 import _native
+
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} not exported"
+    assert sorted(_native.EXPORTED) == sorted(declared_functions())
+
+
+def test_version_and_error_string_without_gpu(lib):
+    assert lib.labs_version() == 100
+    assert lib.labs_last_error() == b""
+
+
+def test_argument_errors_without_gpu(lib):
+    """Argument checks run before any device work, so they answer on a CPU machine."""
+    from paper_2504_00987_gb300 import _native as nat
+
+    assert lib.labs_energy_batch(None, 2, 1, None, None, None) == nat.LABS_EINVAL
+    assert b"N=2" in lib.labs_last_error()
+    assert lib.labs_energy_batch(None, 257, 1, None, None, None) == nat.LABS_EINVAL
+    assert lib.labs_energy_batch(None, 64, -1, None, None, None) == nat.LABS_EINVAL
+    assert lib.labs_energy_batch(None, 64, 0, None, None, None) == nat.LABS_OK  # empty batch
+    P = nat.Params(64, 100, 0, 0, 0, -1, -1, -1, -1, 0, None, 0)  # no budget at all
+    res = (nat.Result * 1)()
+    assert lib.labs_mts_run(ctypes.byref(P), 0, 0, 1, res, None) == nat.LABS_EINVAL
+    assert b"unbounded" in lib.labs_last_error()
+    P.max_steps, P.max_iter = 100, 0  # steps never advance
+    assert lib.labs_mts_run(ctypes.byref(P), 0, 0, 1, res, None) == nat.LABS_EINVAL
+    P.max_iter, P.K = -1, 0
+    assert lib.labs_mts_run(ctypes.byref(P), 0, 0, 1, res, None) == nat.LABS_EINVAL
+    P.K, P.replace_policy = 100, 7
+    assert lib.labs_mts_run(ctypes.byref(P), 0, 0, 1, res, None) == nat.LABS_EINVAL
+    P.replace_policy = 0
+    assert lib.labs_mts_run(ctypes.byref(P), 0, 2**32 - 1, 2, res, None) == nat.LABS_EINVAL
+    assert lib.labs_mts_run(ctypes.byref(P), 0, 0, 0, res, None) == nat.LABS_OK  # no replicas
+    opts = nat.TabuOpts(-2, 0, 0, 0)
+    assert lib.labs_tabu_run(None, 64, 1, 0, ctypes.byref(opts), None, None, None, None, None) == nat.LABS_EINVAL
+
+
+def test_struct_sizes():
+    from paper_2504_00987_gb300 import _native as nat
+
+    assert ctypes.sizeof(nat.DeviceResult) == 64
+    assert ctypes.sizeof(nat.Params) == 4 * 6 + 8 * 2 + 4 * 2 + 8 + 8
+    assert ctypes.sizeof(nat.TabuOpts) == 24
+
+
+def test_no_oracle_in_product():
+    """The product package never imports or links the oracle."""
+    pkg = os.path.join(ROOT, "paper_2504_00987_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "labs_oracle" not in text, f
