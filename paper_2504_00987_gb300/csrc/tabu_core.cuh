@@ -86,6 +86,153 @@ struct TabuOut {
     int32_t E_best;
 };
 
+// Bit-plane count bound: |C_k| <= N - 1 < 32*NW, so C_k fits in
+// bitlen(32*NW - 1) + 1 two's-complement bits.
+template <int NW>
+struct PlaneMax {
+    static constexpr int value = (NW == 2) ? 7 : (NW == 4) ? 8 : 9;
+};
+
+// sum_i popc(w[i]) * weight for n words, carry-save compressed: full
+// adders (sum = a^b^c, carry = maj(a,b,c), one LOP3 each) fold three words
+// of one weight into one word of that weight and one of twice the weight,
+// so n words cost about n/2 + log n popcounts instead of n.
+template <int n, int weight>
+__device__ __forceinline__ int csa_popc(const uint32_t (&w)[n]) {
+    if constexpr (n <= 2) {
+        int s = 0;
+#pragma unroll
+        for (int i = 0; i < n; ++i) s += __popc(w[i]);
+        return s * weight;
+    } else {
+        constexpr int f = (n - 1) / 2;  // full adders at this weight
+        uint32_t carry[f];
+        uint32_t acc = w[0];
+#pragma unroll
+        for (int i = 0; i < f; ++i) {
+            const uint32_t a = acc, b = w[1 + 2 * i], c = w[2 + 2 * i];
+            acc = a ^ b ^ c;
+            carry[i] = (a & b) | (c & (a | b));
+        }
+        int s = __popc(acc);
+        if constexpr (n - 2 * f == 2) s += __popc(w[n - 1]);
+        return s * weight + csa_popc<f, 2 * weight>(carry);
+    }
+}
+
+// S[q] += sum over planes m < P of w_m [popc(t_m & X_q) + popc(t_m & Y_q)],
+// plane 0 being the constant parity pattern of C_k (C_k = N - k mod 2) and
+// plane P-1 the sign plane (weight -2^(P-1)).  Fully unrolled for a
+// compile-time P so every ballot and popcount of the step can overlap.
+template <int NW, int P>
+__device__ __forceinline__ void score_planes(const int32_t (&c)[NW], const uint32_t (&par)[NW],
+                                             const uint32_t (&X)[NW][NW],
+                                             const uint32_t (&Y)[NW][NW], int32_t (&S)[NW]) {
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+        uint32_t tp[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) tp[w] = (m == 0) ? par[w] : __ballot_sync(kFull, (c[w] >> m) & 1);
+        constexpr int32_t one = 1;
+        const int32_t wm = (m == P - 1) ? -(one << m) : (one << m);
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+            uint32_t words[NW + 1];  // (NW - q) words of X_j and (q + 1) of Y_j
+#pragma unroll
+            for (int w = 0; w + q < NW; ++w) words[w] = tp[w] & X[q][w];
+#pragma unroll
+            for (int w = 0; w <= q; ++w) words[NW - q + w] = tp[w] & Y[q][w];
+            S[q] += csa_popc<NW + 1, 1>(words) * wm;
+        }
+    }
+}
+
+// T_j = PC(j) + PC(N-1-j) = Total + sum_{i=1}^{j} (C_i - C_{N-i}) for the
+// lane's j = lane + 32q.  Two chunks are scanned together in one 32-bit
+// value (low and high 16-bit halves): every within-chunk prefix is bounded
+// by 32 * 2 * (N-1) < 2^15.
+template <int NW>
+__device__ __forceinline__ void prefix_terms(const int32_t (&c)[NW], int N, int lane,
+                                             int32_t* __restrict__ Cs, int32_t (&T)[NW]) {
+#pragma unroll
+    for (int q = 0; q < NW; ++q) Cs[lane + 32 * q] = c[q];
+    __syncwarp();
+    int32_t tot = 0;
+    int32_t D[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        const int i = lane + 32 * q;
+        const bool in = i >= 1 && i <= N - 1;
+        D[q] = in ? c[q] - Cs[in ? N - i : 0] : 0;
+        tot += c[q];
+    }
+    __syncwarp();
+    int32_t carry = __reduce_add_sync(kFull, tot);
+#pragma unroll
+    for (int q = 0; q < NW; q += 2) {
+        int32_t v = D[q] + D[q + 1] * 65536;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t n = __shfl_up_sync(kFull, v, o);
+            if (lane >= o) v += n;
+        }
+        const int32_t last = __shfl_sync(kFull, v, 31);
+        const int32_t lo = static_cast<int32_t>(static_cast<int16_t>(v & 0xFFFF));
+        const int32_t hi = (v - lo) / 65536;
+        const int32_t lo31 = static_cast<int32_t>(static_cast<int16_t>(last & 0xFFFF));
+        const int32_t hi31 = (last - lo31) / 65536;
+        T[q] = carry + lo;
+        T[q + 1] = carry + lo31 + hi;
+        carry += lo31 + hi31;
+    }
+}
+
+// Scores every neighbour of the pivot: S_j on P bit planes and T_j from the
+// packed scan, in one block so the two independent chains overlap.
+template <int NW, int P>
+__device__ __forceinline__ void score_all(const int32_t (&c)[NW], const uint32_t (&par)[NW],
+                                          const uint32_t (&X)[NW][NW], const uint32_t (&Y)[NW][NW],
+                                          int N, int lane, int32_t* __restrict__ Cs,
+                                          int32_t (&S)[NW], int32_t (&T)[NW]) {
+#pragma unroll
+    for (int q = 0; q < NW; ++q) S[q] = 0;
+    prefix_terms<NW>(c, N, lane, Cs, T);
+    score_planes<NW, P>(c, par, X, Y, S);
+}
+
+template <int NW>
+__device__ __forceinline__ void score_dispatch(int P, const int32_t (&c)[NW],
+                                               const uint32_t (&par)[NW],
+                                               const uint32_t (&X)[NW][NW],
+                                               const uint32_t (&Y)[NW][NW], int N, int lane,
+                                               int32_t* __restrict__ Cs, int32_t (&S)[NW],
+                                               int32_t (&T)[NW]) {
+    switch (P) {
+        case 2: score_all<NW, 2>(c, par, X, Y, N, lane, Cs, S, T); break;
+        case 3: score_all<NW, 3>(c, par, X, Y, N, lane, Cs, S, T); break;
+        case 4: score_all<NW, 4>(c, par, X, Y, N, lane, Cs, S, T); break;
+        case 5: score_all<NW, 5>(c, par, X, Y, N, lane, Cs, S, T); break;
+        case 6: score_all<NW, 6>(c, par, X, Y, N, lane, Cs, S, T); break;
+        case 7: score_all<NW, 7>(c, par, X, Y, N, lane, Cs, S, T); break;
+        case 8:
+            if constexpr (PlaneMax<NW>::value >= 8) score_all<NW, 8>(c, par, X, Y, N, lane, Cs, S, T);
+            break;
+        default:
+            if constexpr (PlaneMax<NW>::value >= 9) score_all<NW, 9>(c, par, X, Y, N, lane, Cs, S, T);
+            break;
+    }
+}
+
+// Number of two's-complement planes that hold every C_k of the warp:
+// bit length of max |C_k| plus the sign bit.
+template <int NW>
+__device__ __forceinline__ int plane_count(const int32_t (&c)[NW]) {
+    uint32_t mx = 0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) mx = max(mx, static_cast<uint32_t>(abs(c[q])));
+    return 33 - __clz(__reduce_max_sync(kFull, mx));
+}
+
 // One tabu search from `seq` (warp-uniform).  On return `seq` holds
 // bestSeqTS.  Draws: step t uses Philox(instance, g, t, 4): x tie, y tenure.
 // `Cs` is warp-private shared scratch of 32*NW ints.  `trace` (nullable)
@@ -115,13 +262,30 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
     }
     int32_t E_best = E;
     int32_t tabu[NW];
+    // Per-search constants: parity plane (bit k set iff 1 <= k <= N-1 and
+    // N - k odd) and the masks of k in [1, min(j, N-1-j)] used by M_j.
+    uint32_t par[NW];
 #pragma unroll
-    for (int q = 0; q < NW; ++q) tabu[q] = 0;
+    for (int w = 0; w < NW; ++w) {
+        const uint32_t alt = ((N - 32 * w) & 1) ? 0x55555555u : 0xAAAAAAAAu;  // (N - k) odd
+        par[w] = alt & word_lowmask(w, N) & (w == 0 ? ~1u : kFull);
+    }
+    uint32_t mmask[NW][NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        tabu[q] = 0;
+        const int j = lane + 32 * q;
+        const int L = min(j, N - 1 - j);
+#pragma unroll
+        for (int w = 0; w <= q && w + q < NW; ++w)
+            mmask[q][w] = word_lowmask(w, L + 1) & (w == 0 ? ~1u : kFull);
+    }
     const int min_t = max_iter / 10;
     const int max_t = (12 * max_iter) / 100;
     const int64_t nsteps = budget < 0 ? max_iter : (budget < max_iter ? budget : max_iter);
     uint32_t rx = 0, ry = 0;
     int64_t steps = 0;
+    int P = plane_count<NW>(c);
 
     for (int t = 1; t <= nsteps; ++t) {
         if (((t - 1) & 31) == 0) {  // draws of steps t .. t+31, one per lane
@@ -129,6 +293,9 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
             rx = r.x;
             ry = r.y;
         }
+        const int src = (t - 1) & 31;
+        const uint32_t u_tie = __shfl_sync(kFull, rx, src);
+        const uint32_t u_ten = __shfl_sync(kFull, ry, src);
         // ---- windows X_j = B >> j and Y_j (bit k = b_{j-k}) for j = lane + 32q
         uint32_t X[NW][NW], Y[NW][NW];
 #pragma unroll
@@ -141,57 +308,9 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
                 Y[q][w] = __funnelshift_r(RL[w + NW - 1 - q], (w + NW - q < NW) ? RL[w + NW - q] : 0u,
                                           31 - lane);
         }
-        // ---- S_j on the bit planes of C_k
-        uint32_t mx = 0;
-#pragma unroll
-        for (int q = 0; q < NW; ++q) mx = max(mx, static_cast<uint32_t>(abs(c[q])));
-        mx = __reduce_max_sync(kFull, mx);
-        const int P = 33 - __clz(mx);
-        int32_t S[NW];
-#pragma unroll
-        for (int q = 0; q < NW; ++q) S[q] = 0;
-        for (int m = 0; m < P; ++m) {
-            uint32_t tp[NW];
-#pragma unroll
-            for (int w = 0; w < NW; ++w) tp[w] = __ballot_sync(kFull, (c[w] >> m) & 1);
-            const int32_t wm = (m == P - 1) ? -(1 << m) : (1 << m);
-#pragma unroll
-            for (int q = 0; q < NW; ++q) {
-                int s = 0;
-#pragma unroll
-                for (int w = 0; w + q < NW; ++w) s += __popc(tp[w] & X[q][w]);
-#pragma unroll
-                for (int w = 0; w <= q; ++w) s += __popc(tp[w] & Y[q][w]);
-                S[q] += s * wm;
-            }
-        }
-        // ---- T_j = Total + sum_{i=1}^{j} (C_i - C_{N-i})
-#pragma unroll
-        for (int q = 0; q < NW; ++q) Cs[lane + 32 * q] = c[q];
-        __syncwarp();
-        int32_t tot = 0;
-        int32_t D[NW];
-#pragma unroll
-        for (int q = 0; q < NW; ++q) {
-            const int i = lane + 32 * q;
-            const bool in = i >= 1 && i <= N - 1;
-            D[q] = in ? c[q] - Cs[in ? N - i : 0] : 0;
-            tot += c[q];
-        }
-        __syncwarp();
-        int32_t carry = __reduce_add_sync(kFull, tot);
-        int32_t T[NW];
-#pragma unroll
-        for (int q = 0; q < NW; ++q) {
-            int32_t v = D[q];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t n = __shfl_up_sync(kFull, v, o);
-                if (lane >= o) v += n;
-            }
-            T[q] = carry + v;
-            carry += __shfl_sync(kFull, v, 31);
-        }
+        // ---- S_j on the bit planes of C_k; T_j from the packed scan
+        int32_t S[NW], T[NW];
+        score_dispatch<NW>(P, c, par, X, Y, N, lane, Cs, S, T);
         // ---- E_j, admissibility (tabu expired or aspiration), candidates
         const int32_t E0 = E + 4 * (N - 1);
         int32_t cand[NW];
@@ -199,13 +318,10 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
 #pragma unroll
         for (int q = 0; q < NW; ++q) {
             const int j = lane + 32 * q;
-            const int L = min(j, N - 1 - j);
             int dm = 0;
 #pragma unroll
-            for (int w = 0; w <= q && w + q < NW; ++w) {
-                const uint32_t mm = word_lowmask(w, L + 1) & (w == 0 ? ~1u : kFull);
-                dm += __popc((X[q][w] ^ Y[q][w]) & mm);
-            }
+            for (int w = 0; w <= q && w + q < NW; ++w) dm += __popc((X[q][w] ^ Y[q][w]) & mmask[q][w]);
+            const int L = min(j, N - 1 - j);
             const int32_t M = L - 2 * dm;
             const int32_t sj = ((B[q] >> lane) & 1u) ? 1 : -1;
             const int32_t Ej = E0 + 8 * M - 4 * sj * (2 * S[q] - T[q]);
@@ -222,21 +338,24 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
             tb[q] = __ballot_sync(kFull, cand[q] == m);
             count += __popc(tb[q]);
         }
-        const int src = (t - 1) & 31;
-        const uint32_t u_tie = __shfl_sync(kFull, rx, src);
-        const uint32_t u_ten = __shfl_sync(kFull, ry, src);
-        int idx = count > 1 ? static_cast<int>((static_cast<uint64_t>(u_tie) * count) >> 32) : 0;
         int p = 0;
-        bool found = false;
+        if (count == 1) {
 #pragma unroll
-        for (int q = 0; q < NW; ++q) {
-            const int pc = __popc(tb[q]);
-            if (!found) {
-                if (idx < pc) {
-                    p = 32 * q + nth_set_bit(tb[q], idx);
-                    found = true;
-                } else {
-                    idx -= pc;
+            for (int q = NW - 1; q >= 0; --q)
+                if (tb[q]) p = 32 * q + __ffs(tb[q]) - 1;
+        } else {
+            int idx = static_cast<int>((static_cast<uint64_t>(u_tie) * count) >> 32);
+            bool found = false;
+#pragma unroll
+            for (int q = 0; q < NW; ++q) {
+                const int pc = __popc(tb[q]);
+                if (!found) {
+                    if (idx < pc) {
+                        p = 32 * q + nth_set_bit(tb[q], idx);
+                        found = true;
+                    } else {
+                        idx -= pc;
+                    }
                 }
             }
         }
@@ -244,15 +363,16 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
         uint32_t Xp[NW], Yp[NW];
         shr_uniform<NW>(B, p, Xp);            // bit k = b_{p+k}
         shr_uniform<NW>(RL, NB - 1 - p, Yp);  // bit k = b_{p-k}
-        const int32_t sp = (Xp[0] & 1u) ? 1 : -1;
+        const int32_t sp2 = (Xp[0] & 1u) ? 2 : -2;
 #pragma unroll
         for (int q = 0; q < NW; ++q) {
             const int k = lane + 32 * q;
             const int32_t bx = (Xp[q] >> lane) & 1u, by = (Yp[q] >> lane) & 1u;
-            const int32_t sx = (k >= 1 && k <= N - 1 - p) ? 2 * bx - 1 : 0;
+            const int32_t sx = (k >= 1 && k + p <= N - 1) ? 2 * bx - 1 : 0;
             const int32_t sy = (k >= 1 && k <= p) ? 2 * by - 1 : 0;
-            c[q] -= 2 * sp * (sx + sy);
+            c[q] -= sp2 * (sx + sy);
         }
+        P = plane_count<NW>(c);  // for the next step; overlaps with the tail below
         flip_bit<NW>(B, p);
         flip_bit<NW>(RL, NB - 1 - p);
         const int32_t expiry = t + rand_int(min_t, max_t, u_ten);
