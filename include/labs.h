@@ -138,6 +138,36 @@ typedef struct labs_tabu_opts {
     int64_t trace_cap;       /* records {g, t, j, E} per sequence in d_trace */
 } labs_tabu_opts;
 
+/*
+ * One Memetic-Tabu instance of a batch (64 bytes, host or device).  The
+ * fields mean what the labs_params fields of the same name mean; the run
+ * of an instance is a pure function of this record, so it is the same
+ * alone, in any batch, under any mapping.  p_mut_u32 == 0 selects
+ * floor(2^32 / N).  `instance` (< 2^32) is counter word 0 of its draws.
+ */
+typedef struct labs_instance {
+    int32_t N, K;
+    uint32_t p_comb_u32, p_mut_u32;
+    int32_t replace_policy, target_E;
+    int64_t max_generations, max_steps;
+    int32_t max_iter, pad;
+    uint64_t seed;
+    uint64_t instance;
+} labs_instance;
+
+#define LABS_ORDER_LPT 0   /* queue longest instance first (pair-term budget) */
+#define LABS_ORDER_GIVEN 1 /* queue in the given order */
+
+/* How a batch is mapped on the GPU. */
+typedef struct labs_mapping {
+    int32_t warps_per_block; /* populations (one per warp) per CTA: 1, 2, 4 or 8 */
+    int32_t blocks_per_sm;   /* resident CTAs per SM of the persistent grid, >= 1 */
+    int32_t order;           /* LABS_ORDER_* */
+    int32_t pad;
+} labs_mapping;
+
+typedef struct labs_batch labs_batch; /* opaque */
+
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char* labs_last_error(void);
 
@@ -195,6 +225,43 @@ int32_t labs_mts_launch(const labs_params* P, uint64_t seed, uint64_t first_inst
  */
 int32_t labs_mts_run(const labs_params* P, uint64_t seed, uint64_t first_instance,
                      int64_t replicas, labs_result* h_out, labs_stream_t stream);
+
+/*
+ * Batched uneven instances: one persistent launch, captured once in a CUDA
+ * graph, in which every warp takes the next instance from a device queue
+ * and runs it to its stop condition.  Every instance must be bounded by a
+ * generation budget or a step budget (with max_iter != 0).
+ *
+ * labs_autotune      -- picks a mapping for these instances by timing the
+ *                       candidate mappings (warps_per_block x blocks_per_sm
+ *                       within occupancy) on a copy of the batch with every
+ *                       budget divided by 8; caches the choice per batch
+ *                       signature.  BLOCKING; uses `stream`.
+ * labs_batch_create  -- validates and orders the instances (host h_inst[n]),
+ *                       uploads them, allocates the results and captures the
+ *                       launch in a CUDA graph.  mapping == NULL: autotune.
+ *                       Allocates device memory (cudaMalloc); BLOCKING.
+ * labs_batch_launch  -- replays the graph on `stream` (asynchronous).  May be
+ *                       called again; each launch reruns every instance.
+ * labs_batch_device_results -- the device array of n labs_device_result, in
+ *                       the original instance order (owned by the batch).
+ * labs_batch_results -- copies the results to h_out[n] (original order) and
+ *                       fills the merit factors.  BLOCKING on `stream`.
+ * labs_batch_get_mapping -- the mapping the batch runs with.
+ * labs_batch_destroy -- frees everything; NULL is a no-op.
+ * labs_mts_batch_run -- create + launch + results + destroy.  BLOCKING.
+ */
+int32_t labs_autotune(const labs_instance* h_inst, int64_t n, labs_stream_t stream,
+                      labs_mapping* out);
+int32_t labs_batch_create(const labs_instance* h_inst, int64_t n, const labs_mapping* mapping,
+                          labs_stream_t stream, labs_batch** out);
+int32_t labs_batch_launch(labs_batch* b, labs_stream_t stream);
+int32_t labs_batch_device_results(const labs_batch* b, labs_device_result** d_out);
+int32_t labs_batch_results(labs_batch* b, labs_result* h_out, labs_stream_t stream);
+int32_t labs_batch_get_mapping(const labs_batch* b, labs_mapping* out);
+int32_t labs_batch_destroy(labs_batch* b);
+int32_t labs_mts_batch_run(const labs_instance* h_inst, int64_t n, const labs_mapping* mapping,
+                           labs_result* h_out, labs_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -13,6 +13,10 @@ from __future__ import annotations
 
 from .api import (  # noqa: F401
     P_COMB_U32,
+    Batch,
+    autotune,
+    make_instance,
+    mts_batch_run,
     decode_results,
     energy_batch,
     mts_launch,

@@ -35,8 +35,12 @@ RUN_STOPPED = 2
 # Every symbol include/labs.h declares.
 EXPORTED = [
     "labs_last_error", "labs_version", "labs_energy_batch", "labs_tabu_run",
-    "labs_mts_launch", "labs_mts_run",
+    "labs_mts_launch", "labs_mts_run", "labs_autotune", "labs_batch_create", "labs_batch_launch",
+    "labs_batch_device_results", "labs_batch_results", "labs_batch_get_mapping",
+    "labs_batch_destroy", "labs_mts_batch_run",
 ]
+ORDER_LPT = 0
+ORDER_GIVEN = 1
 
 
 class LabsError(RuntimeError):
@@ -99,7 +103,34 @@ class TabuOpts(ctypes.Structure):
     ]
 
 
+class Instance(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int32),
+        ("K", ctypes.c_int32),
+        ("p_comb_u32", ctypes.c_uint32),
+        ("p_mut_u32", ctypes.c_uint32),
+        ("replace_policy", ctypes.c_int32),
+        ("target_E", ctypes.c_int32),
+        ("max_generations", ctypes.c_int64),
+        ("max_steps", ctypes.c_int64),
+        ("max_iter", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("instance", ctypes.c_uint64),
+    ]
+
+
+class Mapping(ctypes.Structure):
+    _fields_ = [
+        ("warps_per_block", ctypes.c_int32),
+        ("blocks_per_sm", ctypes.c_int32),
+        ("order", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+    ]
+
+
 assert ctypes.sizeof(DeviceResult) == 64
+assert ctypes.sizeof(Instance) == 64
 
 _lock = threading.Lock()
 _lib = None
@@ -129,6 +160,23 @@ def load(path: str = LIB_PATH):
         L.labs_mts_launch.argtypes = [ctypes.POINTER(Params), u64, u64, i64, vp, vp, vp]
         L.labs_mts_run.restype = i32
         L.labs_mts_run.argtypes = [ctypes.POINTER(Params), u64, u64, i64, ctypes.POINTER(Result), vp]
+        IP, MP, RP = ctypes.POINTER(Instance), ctypes.POINTER(Mapping), ctypes.POINTER(Result)
+        L.labs_autotune.restype = i32
+        L.labs_autotune.argtypes = [IP, i64, vp, MP]
+        L.labs_batch_create.restype = i32
+        L.labs_batch_create.argtypes = [IP, i64, MP, vp, ctypes.POINTER(vp)]
+        L.labs_batch_launch.restype = i32
+        L.labs_batch_launch.argtypes = [vp, vp]
+        L.labs_batch_device_results.restype = i32
+        L.labs_batch_device_results.argtypes = [vp, ctypes.POINTER(vp)]
+        L.labs_batch_results.restype = i32
+        L.labs_batch_results.argtypes = [vp, RP, vp]
+        L.labs_batch_get_mapping.restype = i32
+        L.labs_batch_get_mapping.argtypes = [vp, MP]
+        L.labs_batch_destroy.restype = i32
+        L.labs_batch_destroy.argtypes = [vp]
+        L.labs_mts_batch_run.restype = i32
+        L.labs_mts_batch_run.argtypes = [IP, i64, MP, RP, vp]
         _lib = L
         return L
 

@@ -129,3 +129,103 @@ def mts_run(params: nat.Params, seed: int, first_instance: int, replicas: int, s
         "status": int(r.status), "generations": int(r.generations), "steps": int(r.steps),
         "flip_evals": int(r.flip_evals), "trace_len": int(r.trace_len), "seconds": float(r.seconds),
     } for r in list(res)[:replicas]]
+
+
+# ---------------------------------------------------------------- batches
+
+
+def make_instance(N: int, K: int = 100, *, seed: int = 0, instance: int = 0, max_steps: int = -1,
+                  max_generations: int = -1, target_E: int = -1, p_comb_u32: int = P_COMB_U32,
+                  p_mut: int = 0, replace_policy: int = nat.REPLACE_RANDOM,
+                  max_iter: int = -1) -> nat.Instance:
+    return nat.Instance(N, K, p_comb_u32, p_mut, replace_policy, target_E, max_generations,
+                        max_steps, max_iter, 0, seed, instance)
+
+
+def _inst_array(instances):
+    n = len(instances)
+    arr = (nat.Instance * max(n, 1))()
+    for i, x in enumerate(instances):
+        arr[i] = x
+    return arr, n
+
+
+def _mapping(mapping):
+    if mapping is None:
+        return None
+    if isinstance(mapping, nat.Mapping):
+        return mapping
+    return nat.Mapping(int(mapping["warps_per_block"]), int(mapping["blocks_per_sm"]),
+                       int(mapping.get("order", nat.ORDER_LPT)), 0)
+
+
+def _mapping_dict(m: nat.Mapping) -> dict:
+    return {"warps_per_block": m.warps_per_block, "blocks_per_sm": m.blocks_per_sm, "order": m.order}
+
+
+def _result_dicts(res, n):
+    return [{
+        "instance": int(r.instance), "N": int(r.N), "seq": list(r.seq)[: words_for(int(r.N))],
+        "E": int(r.E), "F": float(r.F), "status": int(r.status), "generations": int(r.generations),
+        "steps": int(r.steps), "flip_evals": int(r.flip_evals), "seconds": float(r.seconds),
+    } for r in list(res)[:n]]
+
+
+def autotune(instances, stream=None) -> dict:
+    """The mapping labs_autotune picks for these instances (cached per batch signature)."""
+    arr, n = _inst_array(instances)
+    m = nat.Mapping()
+    nat.check(nat.load().labs_autotune(arr, n, _stream(stream), ctypes.byref(m)))
+    return _mapping_dict(m)
+
+
+class Batch:
+    """A captured persistent launch over uneven instances (labs_batch_*)."""
+
+    def __init__(self, instances, mapping=None, stream=None):
+        arr, self.n = _inst_array(instances)
+        self._h = ctypes.c_void_p()
+        m = _mapping(mapping)
+        nat.check(nat.load().labs_batch_create(arr, self.n, ctypes.byref(m) if m is not None else None,
+                                               _stream(stream), ctypes.byref(self._h)))
+
+    @property
+    def mapping(self) -> dict:
+        m = nat.Mapping()
+        nat.check(nat.load().labs_batch_get_mapping(self._h, ctypes.byref(m)))
+        return _mapping_dict(m)
+
+    def launch(self, stream=None) -> None:
+        nat.check(nat.load().labs_batch_launch(self._h, _stream(stream)))
+
+    def results(self, stream=None) -> list[dict]:
+        res = (nat.Result * max(self.n, 1))()
+        nat.check(nat.load().labs_batch_results(self._h, res, _stream(stream)))
+        return _result_dicts(res, self.n)
+
+    def close(self) -> None:
+        if self._h:
+            nat.load().labs_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mts_batch_run(instances, mapping=None, stream=None) -> list[dict]:
+    """Blocking: create, launch, collect and destroy a batch."""
+    arr, n = _inst_array(instances)
+    res = (nat.Result * max(n, 1))()
+    m = _mapping(mapping)
+    nat.check(nat.load().labs_mts_batch_run(arr, n, ctypes.byref(m) if m is not None else None, res,
+                                            _stream(stream)))
+    return _result_dicts(res, n)

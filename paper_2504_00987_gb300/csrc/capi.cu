@@ -9,10 +9,11 @@
 #include <cstring>
 #include <vector>
 
+#include "capi_util.h"
 #include "kernels.h"
 #include "labs.h"
 
-namespace {
+namespace lcapi {
 
 thread_local char g_err[512] = {0};
 
@@ -38,13 +39,13 @@ bool is_device_ptr(const void* p) {
     if (p == nullptr) return false;
     cudaPointerAttributes attr;
     if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
-        cudaGetLastError();  // clear the sticky-free error of the query
+        cudaGetLastError();  // clear the error state of the failed query
         return false;
     }
     return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
-bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 int32_t check_dev(const void* p, size_t align, const char* name, bool nullable) {
     if (p == nullptr) return nullable ? LABS_OK : fail(LABS_EINVAL, "%s is NULL", name);
@@ -53,41 +54,79 @@ int32_t check_dev(const void* p, size_t align, const char* name, bool nullable) 
     return LABS_OK;
 }
 
-#define LABS_TRY(expr)                      \
-    do {                                    \
-        const int32_t rc_ = (expr);         \
-        if (rc_ != LABS_OK) return rc_;     \
-    } while (0)
-
 int32_t check_N(int32_t N) {
     if (N < 3 || N > LABS_MAX_N) return fail(LABS_EINVAL, "N=%d outside 3..%d", N, LABS_MAX_N);
     return LABS_OK;
 }
 
+int32_t check_run(int32_t N, int32_t K, int32_t replace_policy, int32_t target_E,
+                  int64_t max_generations, int64_t max_steps, int32_t max_iter, uint64_t first_instance,
+                  int64_t count, const char* who) {
+    if (N < 3 || N > LABS_MAX_N) return fail(LABS_EINVAL, "%s: N=%d outside 3..%d", who, N, LABS_MAX_N);
+    if (K < 1 || K > LABS_MAX_K) return fail(LABS_EINVAL, "%s: K=%d outside 1..%d", who, K, LABS_MAX_K);
+    if (replace_policy != LABS_REPLACE_RANDOM && replace_policy != LABS_REPLACE_WORST)
+        return fail(LABS_EINVAL, "%s: unknown replace_policy %d", who, replace_policy);
+    if (max_iter < -1 || max_iter > (1 << 20))
+        return fail(LABS_EINVAL, "%s: max_iter=%d outside -1..2^20", who, max_iter);
+    if (target_E < -1) return fail(LABS_EINVAL, "%s: target_E=%d (use -1 for none)", who, target_E);
+    if (max_generations < -1 || max_steps < -1)
+        return fail(LABS_EINVAL, "%s: budgets must be -1 (unlimited) or >= 0", who);
+    // Every run must end: a generation budget, or a step budget with steps
+    // that advance.  Generation numbers index the Philox counter (32 bits).
+    const bool gen_bound = max_generations >= 0;
+    const bool step_bound = max_steps >= 0 && max_iter != 0;
+    if (!gen_bound && !step_bound)
+        return fail(LABS_EINVAL,
+                    "%s: unbounded run: set max_generations, or max_steps with max_iter != 0", who);
+    if ((gen_bound ? max_generations : max_steps) > 0xFFFFFFFFll)
+        return fail(LABS_EINVAL, "%s: more than 2^32 - 1 generations possible", who);
+    if (count < 0) return fail(LABS_EINVAL, "%s: negative count", who);
+    if (first_instance + static_cast<uint64_t>(count) > 0x100000000ull)
+        return fail(LABS_EINVAL, "%s: instances beyond 2^32 - 1", who);
+    if (lgpu::mts_smem_per_warp(N, K) > 227u * 1024u)
+        return fail(LABS_EINVAL, "%s: population does not fit in shared memory (N=%d, K=%d)", who, N, K);
+    return LABS_OK;
+}
+
+uint32_t default_p_mut(int32_t N, uint32_t p_mut_u32) {
+    return p_mut_u32 != 0 ? p_mut_u32 : static_cast<uint32_t>((1ull << 32) / N);
+}
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+void fill_host_result(const labs_device_result& d, int32_t N, uint64_t instance, double seconds,
+                      labs_result* o) {
+    memcpy(o->seq, d.seq, sizeof o->seq);
+    o->E = d.E;
+    o->N = N;
+    o->F = d.E > 0 ? static_cast<double>(N) * N / (2.0 * d.E) : 0.0;
+    o->generations = d.generations;
+    o->steps = d.steps;
+    o->flip_evals = d.steps * N;
+    o->trace_len = d.trace_len;
+    o->instance = instance;
+    o->seconds = seconds;
+    o->status = d.status;
+    o->pad = 0;
+}
+
+}  // namespace lcapi
+
+namespace {
+
+using namespace lcapi;
+
 // Validates P and fills the kernel arguments (everything except pointers).
 int32_t make_mts_args(const labs_params* P, uint64_t seed, uint64_t first_instance,
                       int64_t replicas, lgpu::MtsArgs* a) {
     if (P == nullptr) return fail(LABS_EINVAL, "params is NULL");
-    LABS_TRY(check_N(P->N));
-    if (P->K < 1 || P->K > LABS_MAX_K) return fail(LABS_EINVAL, "K=%d outside 1..%d", P->K, LABS_MAX_K);
-    if (P->replace_policy != LABS_REPLACE_RANDOM && P->replace_policy != LABS_REPLACE_WORST)
-        return fail(LABS_EINVAL, "unknown replace_policy %d", P->replace_policy);
-    if (P->max_iter < -1 || P->max_iter > (1 << 20))
-        return fail(LABS_EINVAL, "max_iter=%d outside -1..2^20", P->max_iter);
-    if (P->target_E < -1) return fail(LABS_EINVAL, "target_E=%d (use -1 for none)", P->target_E);
-    if (P->max_generations < -1 || P->max_steps < -1)
-        return fail(LABS_EINVAL, "budgets must be -1 (unlimited) or >= 0");
-    // Every run must end: a generation budget, or a step budget with steps
-    // that advance.  Generation numbers index the Philox counter (32 bits).
-    const bool gen_bound = P->max_generations >= 0;
-    const bool step_bound = P->max_steps >= 0 && P->max_iter != 0;
-    if (!gen_bound && !step_bound)
-        return fail(LABS_EINVAL, "unbounded run: set max_generations, or max_steps with max_iter != 0");
-    if ((gen_bound ? P->max_generations : P->max_steps) > 0xFFFFFFFFll)
-        return fail(LABS_EINVAL, "more than 2^32 - 1 generations possible");
-    if (replicas < 0) return fail(LABS_EINVAL, "replicas=%lld < 0", static_cast<long long>(replicas));
-    if (first_instance + static_cast<uint64_t>(replicas) > 0x100000000ull)
-        return fail(LABS_EINVAL, "instances beyond 2^32 - 1");
+    LABS_TRY(check_run(P->N, P->K, P->replace_policy, P->target_E, P->max_generations, P->max_steps,
+                       P->max_iter, first_instance, replicas, "params"));
     if (replicas > (static_cast<int64_t>(1) << 31) * lgpu::kWarpsPerBlock / 2)
         return fail(LABS_EINVAL, "too many replicas for one launch");
     if (P->trace_cap < 0) return fail(LABS_EINVAL, "trace_cap < 0");
@@ -99,7 +138,7 @@ int32_t make_mts_args(const labs_params* P, uint64_t seed, uint64_t first_instan
     a->N = P->N;
     a->K = P->K;
     a->p_comb_u32 = P->p_comb_u32;
-    a->p_mut_u32 = P->p_mut_u32 != 0 ? P->p_mut_u32 : static_cast<uint32_t>((1ull << 32) / P->N);
+    a->p_mut_u32 = default_p_mut(P->N, P->p_mut_u32);
     a->replace_policy = P->replace_policy;
     a->target_E = P->target_E;
     a->max_generations = P->max_generations;
@@ -120,7 +159,7 @@ int32_t make_mts_args(const labs_params* P, uint64_t seed, uint64_t first_instan
 
 extern "C" {
 
-const char* labs_last_error(void) { return g_err; }
+const char* labs_last_error(void) { return lcapi::g_err; }
 
 int32_t labs_version(void) { return 100; }
 
@@ -222,22 +261,9 @@ int32_t labs_mts_run(const labs_params* P, uint64_t seed, uint64_t first_instanc
     if (es != cudaSuccess) return cuda_fail(es, "labs_mts_run synchronize");
     const double secs =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    for (int64_t r = 0; r < replicas; ++r) {
-        const labs_device_result& d = host[static_cast<size_t>(r)];
-        labs_result& o = h_out[r];
-        memcpy(o.seq, d.seq, sizeof o.seq);
-        o.E = d.E;
-        o.N = P->N;
-        o.F = d.E > 0 ? static_cast<double>(P->N) * P->N / (2.0 * d.E) : 0.0;
-        o.generations = d.generations;
-        o.steps = d.steps;
-        o.flip_evals = d.steps * P->N;
-        o.trace_len = d.trace_len;
-        o.instance = first_instance + static_cast<uint64_t>(r);
-        o.seconds = secs;
-        o.status = d.status;
-        o.pad = 0;
-    }
+    for (int64_t r = 0; r < replicas; ++r)
+        fill_host_result(host[static_cast<size_t>(r)], P->N, first_instance + static_cast<uint64_t>(r),
+                         secs, &h_out[r]);
     return ok();
 }
 

@@ -1,0 +1,35 @@
+// capi_util.h -- argument checks and error reporting shared by the C ABI
+// translation units (internal; not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "labs.h"
+
+namespace lcapi {
+
+int32_t fail(int32_t code, const char* fmt, ...);
+int32_t ok();
+int32_t cuda_fail(cudaError_t e, const char* what);
+bool is_device_ptr(const void* p);
+int32_t check_dev(const void* p, size_t align, const char* name, bool nullable);
+int32_t check_N(int32_t N);
+// Validates the run parameters shared by labs_params and labs_instance.
+int32_t check_run(int32_t N, int32_t K, int32_t replace_policy, int32_t target_E,
+                  int64_t max_generations, int64_t max_steps, int32_t max_iter, uint64_t first_instance,
+                  int64_t count, const char* who);
+uint32_t default_p_mut(int32_t N, uint32_t p_mut_u32);
+int sm_count();
+void fill_host_result(const labs_device_result& d, int32_t N, uint64_t instance, double seconds,
+                      labs_result* o);
+
+}  // namespace lcapi
+
+#define LABS_TRY(expr)                  \
+    do {                                \
+        const int32_t rc_ = (expr);     \
+        if (rc_ != LABS_OK) return rc_; \
+    } while (0)

@@ -41,7 +41,19 @@ struct TabuArgs {
     int64_t trace_cap;
 };
 
+struct BatchArgs {
+    const labs_instance* inst;     // queue order
+    const int32_t* order;          // queue position -> original index
+    int64_t n;
+    labs_device_result* out;       // original order
+    unsigned long long* queue;     // next queue position
+    size_t smem_per_warp;
+};
+
 size_t mts_smem_per_warp(int N, int K);
+cudaError_t batch_prepare(int nwmax, int warps_per_block, size_t smem_per_warp, int* max_blocks_per_sm);
+cudaError_t launch_batch(const BatchArgs& a, int nwmax, int blocks, int warps_per_block,
+                         cudaStream_t stream);
 cudaError_t launch_mts(const MtsArgs& a, cudaStream_t stream);
 cudaError_t launch_tabu(const TabuArgs& a, cudaStream_t stream);
 cudaError_t launch_energy(const uint64_t* d_seqs, int N, int64_t B, int32_t* d_E, int32_t* d_C,

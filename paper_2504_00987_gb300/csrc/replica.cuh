@@ -1,0 +1,233 @@
+// replica.cuh -- one warp runs one Memetic-Tabu replica (Algorithm 1 /
+// Algorithm 3): initial population, the generation step (selection,
+// crossover or sampling, mutation, tabu search, best update, replacement)
+// and the stop test.  The population (K packed sequences and their
+// energies) lives in the warp's slice of shared memory; everything else in
+// registers.  The functions are split at generation boundaries so a replica
+// can also be suspended and resumed there (the state between generations
+// is the population, the best sequence and the counters).
+#pragma once
+
+#include "tabu_core.cuh"
+
+namespace lgpu {
+
+// Parameters of one replica (an MTS instance under one Philox stream).
+struct ReplicaCfg {
+    int32_t N, K;
+    uint32_t p_comb_u32, p_mut_u32;
+    int32_t replace_policy, target_E;
+    int64_t max_generations, max_steps;
+    int32_t max_iter;
+    uint32_t inst;
+    uint2 key;
+};
+
+template <int NW>
+struct ReplicaState {
+    uint32_t best[NW];
+    int32_t E_best;
+    int32_t status;
+    int64_t g, steps;
+};
+
+template <int NW>
+__device__ __forceinline__ void load_seq(const uint32_t* __restrict__ src, uint32_t (&v)[NW]) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) v[w] = src[w];
+}
+
+// Lane w < NW writes word w of a warp-uniform sequence.
+template <int NW>
+__device__ __forceinline__ void store_seq(uint32_t* __restrict__ dst, const uint32_t (&v)[NW], int lane) {
+    if (lane < NW) {
+        uint32_t x = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) x = (lane == w) ? v[w] : x;
+        dst[lane] = x;
+    }
+}
+
+// Binary tournament: the lower energy wins, the lower index on ties.
+__device__ __forceinline__ int tournament(const int32_t* __restrict__ popE, int a, int b) {
+    const int32_t ea = popE[a], eb = popE[b];
+    if (ea < eb) return a;
+    if (eb < ea) return b;
+    return a < b ? a : b;
+}
+
+// population <- K random sequences (word w of member p from Philox
+// (inst, p, w/2, INIT)); bestSeq <- the lowest energy, lowest index on ties.
+template <int NW>
+__device__ void replica_init(const ReplicaCfg& a, uint32_t* __restrict__ pop,
+                             int32_t* __restrict__ popE, ReplicaState<NW>& st, int lane) {
+    const int N = a.N, K = a.K;
+    for (int idx = lane; idx < K * (NW / 2); idx += 32) {
+        const int p = idx / (NW / 2), w64 = idx % (NW / 2);
+        const uint4 d = draw4(a.key, a.inst, static_cast<uint32_t>(p), static_cast<uint32_t>(w64), kPurposeInit);
+        pop[p * NW + 2 * w64] = d.x & word_lowmask(2 * w64, N);
+        pop[p * NW + 2 * w64 + 1] = d.y & word_lowmask(2 * w64 + 1, N);
+    }
+    __syncwarp();
+    int32_t lbestE = INT_MAX;
+    int lbest = INT_MAX;
+    for (int p = lane; p < K; p += 32) {
+        uint32_t B[NW];
+        load_seq<NW>(pop + p * NW, B);
+        const int32_t e = thread_energy<NW>(B, N);
+        popE[p] = e;
+        if (e < lbestE) {
+            lbestE = e;
+            lbest = p;
+        }
+    }
+    __syncwarp();
+    st.E_best = __reduce_min_sync(kFull, lbestE);
+    const int best0 = __reduce_min_sync(kFull, lbestE == st.E_best ? lbest : INT_MAX);
+    load_seq<NW>(pop + best0 * NW, st.best);
+    st.status = LABS_RUN_BUDGET;
+    st.g = 0;
+    st.steps = 0;
+}
+
+// The while-condition of Algorithm 1 plus the budgets and the GLF of
+// Algorithm 3.  True if the replica stops before generation st.g.
+template <int NW>
+__device__ __forceinline__ bool replica_should_stop(const ReplicaCfg& a, ReplicaState<NW>& st,
+                                                    const uint32_t* glf) {
+    if (a.target_E >= 0 && st.E_best <= a.target_E) {
+        st.status = LABS_RUN_REACHED;
+        return true;
+    }
+    if (a.max_generations >= 0 && st.g >= a.max_generations) return true;
+    if (a.max_steps >= 0 && st.steps >= a.max_steps) return true;
+    if (glf != nullptr) {
+        const uint32_t f = __shfl_sync(kFull, *reinterpret_cast<const volatile uint32_t*>(glf), 0);
+        if (f != 0u) {
+            st.status = LABS_RUN_STOPPED;
+            return true;
+        }
+    }
+    return false;
+}
+
+// One generation g = st.g.  Returns the tabu steps it took.
+template <int NW>
+__device__ int64_t replica_generation(const ReplicaCfg& a, ReplicaState<NW>& st,
+                                      uint32_t* __restrict__ pop, int32_t* __restrict__ popE,
+                                      int32_t* __restrict__ Cs, int4* __restrict__ trace,
+                                      int64_t trace_cap, int64_t& trace_len, uint32_t* glf,
+                                      int lane) {
+    const int N = a.N, K = a.K;
+    const uint32_t gg = static_cast<uint32_t>(st.g);
+    const uint32_t p_mut = a.p_mut_u32;
+    // generation draws: lane 0 -> (g,0), lane 1 -> (g,1), lane 2 -> (g,2)
+    const uint4 gd = draw4(a.key, a.inst, gg, static_cast<uint32_t>(lane < 3 ? lane : 0), kPurposeGen);
+    const uint32_t coin = __shfl_sync(kFull, gd.x, 0);
+    const uint32_t ua = __shfl_sync(kFull, gd.y, 0), ub = __shfl_sync(kFull, gd.z, 0);
+    const uint32_t uc = __shfl_sync(kFull, gd.w, 0), ud = __shfl_sync(kFull, gd.x, 1);
+    const uint32_t ucut = __shfl_sync(kFull, gd.y, 1), usamp = __shfl_sync(kFull, gd.z, 1);
+    const uint32_t uiter = __shfl_sync(kFull, gd.w, 1), urep = __shfl_sync(kFull, gd.x, 2);
+
+    uint32_t child[NW];
+    if (coin < a.p_comb_u32) {
+        const int p1 = tournament(popE, rand_int(0, K - 1, ua), rand_int(0, K - 1, ub));
+        const int p2 = tournament(popE, rand_int(0, K - 1, uc), rand_int(0, K - 1, ud));
+        const int cut = rand_int(1, N - 1, ucut);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t lm = word_lowmask(w, cut);
+            child[w] = (pop[p1 * NW + w] & lm) | (pop[p2 * NW + w] & ~lm);
+        }
+    } else {
+        load_seq<NW>(pop + rand_int(0, K - 1, usamp) * NW, child);
+    }
+    // Mutate: bit j flips iff word j%4 of (inst, g, j/4, MUT) < p_mut.
+    const int nmut = (N + 3) / 4;
+    for (int base = 0; base < nmut; base += 32) {
+        const int cidx = base + lane;
+        uint32_t nib = 0;
+        if (cidx < nmut) {
+            const uint4 d = draw4(a.key, a.inst, gg, static_cast<uint32_t>(cidx), kPurposeMut);
+            nib = (d.x < p_mut ? 1u : 0u) | (d.y < p_mut ? 2u : 0u) | (d.z < p_mut ? 4u : 0u) |
+                  (d.w < p_mut ? 8u : 0u);
+        }
+        const int word_of = cidx >> 3;  // 8 nibbles per 32-bit word
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t part = (word_of == w) ? (nib << (4 * (cidx & 7))) : 0u;
+            child[w] ^= __reduce_or_sync(kFull, part) & word_lowmask(w, N);
+        }
+    }
+    // child <- Tabu-Search(child)
+    const int max_iter = a.max_iter >= 0 ? a.max_iter : N / 2 + rand_int(0, N, uiter);
+    const int64_t budget = a.max_steps >= 0 ? a.max_steps - st.steps : -1;
+    const TabuOut to = tabu_search<NW>(child, N, a.key, a.inst, gg, max_iter, budget, Cs, trace,
+                                       trace_cap, trace_len, lane);
+    st.steps += to.steps;
+    if (to.E_best < st.E_best) {
+        st.E_best = to.E_best;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) st.best[w] = child[w];
+    }
+    // replace a member of the population by the child
+    int slot;
+    if (a.replace_policy == LABS_REPLACE_RANDOM) {
+        slot = rand_int(0, K - 1, urep);
+    } else {
+        int32_t lmax = INT_MIN;
+        for (int p = lane; p < K; p += 32) lmax = max(lmax, popE[p]);
+        const int32_t emax = __reduce_max_sync(kFull, lmax);
+        int lidx = INT_MAX;
+        for (int p = lane; p < K; p += 32)
+            if (popE[p] == emax) {
+                lidx = p;
+                break;
+            }
+        slot = __reduce_min_sync(kFull, lidx);
+    }
+    __syncwarp();
+    store_seq<NW>(pop + slot * NW, child, lane);
+    if (lane == 0) popE[slot] = to.E_best;
+    __syncwarp();
+    if (trace != nullptr && trace_len < trace_cap) {
+        if (lane == 0) trace[trace_len] = make_int4(static_cast<int>(st.g), 0, slot, to.E_best);
+        ++trace_len;
+    }
+    ++st.g;
+    if (glf != nullptr && a.target_E >= 0 && to.E_best <= a.target_E && lane == 0) atomicExch(glf, 1u);
+    return to.steps;
+}
+
+template <int NW>
+__device__ __forceinline__ void replica_store_result(const ReplicaState<NW>& st, int64_t trace_len,
+                                                     labs_device_result* out, int lane) {
+    if (lane < 2 * LABS_MAX_W) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) v = (lane == w) ? st.best[w] : v;
+        reinterpret_cast<uint32_t*>(out->seq)[lane] = v;
+    }
+    if (lane == 0) {
+        out->E = st.E_best;
+        out->status = st.status;
+        out->generations = st.g;
+        out->steps = st.steps;
+        out->trace_len = trace_len;
+    }
+}
+
+// A whole replica from scratch to its stop condition.
+template <int NW>
+__device__ __forceinline__ void replica_run(const ReplicaCfg& a, uint32_t* pop, int32_t* popE,
+                                            int32_t* Cs, int4* trace, int64_t trace_cap,
+                                            uint32_t* glf, labs_device_result* out, int lane) {
+    ReplicaState<NW> st;
+    int64_t trace_len = 0;
+    replica_init<NW>(a, pop, popE, st, lane);
+    while (!replica_should_stop<NW>(a, st, glf))
+        replica_generation<NW>(a, st, pop, popE, Cs, trace, trace_cap, trace_len, glf, lane);
+    replica_store_result<NW>(st, trace_len, out, lane);
+}
+
+}  // namespace lgpu

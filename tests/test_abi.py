@@ -90,3 +90,19 @@ def test_no_oracle_in_product():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "labs_oracle" not in text, f
+
+
+def test_batch_argument_errors_without_gpu(lib):
+    from paper_2504_00987_gb300 import _native as nat
+
+    arr = (nat.Instance * 2)()
+    arr[0] = nat.Instance(64, 100, 0, 0, 0, -1, -1, 100, -1, 0, 0, 0)
+    arr[1] = nat.Instance(64, 100, 0, 0, 0, -1, -1, -1, -1, 0, 0, 1)  # unbounded
+    m = nat.Mapping()
+    assert lib.labs_autotune(arr, 2, None, ctypes.byref(m)) == nat.LABS_EINVAL
+    assert b"instance 1" in lib.labs_last_error()
+    h = ctypes.c_void_p()
+    bad_map = nat.Mapping(3, 1, 0, 0)
+    arr[1].max_steps = 10
+    assert lib.labs_batch_create(arr, 2, ctypes.byref(bad_map), None, ctypes.byref(h)) == nat.LABS_EINVAL
+    assert lib.labs_batch_destroy(None) == nat.LABS_OK
