@@ -263,6 +263,31 @@ int32_t labs_batch_destroy(labs_batch* b);
 int32_t labs_mts_batch_run(const labs_instance* h_inst, int64_t n, const labs_mapping* mapping,
                            labs_result* h_out, labs_stream_t stream);
 
+/*
+ * labs_mts_run_static -- labs_mts_run without any memory allocation (no
+ * counterpart in the paper; an interface for callers that cannot allocate).
+ * Some callers may not allocate device memory at all: an application that
+ * owns the GPU memory budget through its own pool, a latency-critical loop
+ * that cannot afford cudaMalloc/cudaFree (which may synchronise the
+ * device), or a process under a hard device-memory quota.  This call makes
+ * no device or host allocation: its device scratch (one result record per
+ * replica and the global termination flag) is a fixed array compiled into
+ * the library, sized for LABS_STATIC_MAX_REPLICAS replicas (about 256 KiB),
+ * which every GPU that loads the library holds until the process exits.
+ *   - replicas > LABS_STATIC_MAX_REPLICAS is rejected with LABS_EINVAL.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls on a device share the one array, which keeps the last
+ *     call's contents (each call clears the flag and overwrites the records
+ *     it reads): calls whose GPU work overlaps -- on different streams or
+ *     from different threads -- race and must be serialised by the caller.
+ *   - Arguments, results and errors are those of labs_mts_run.  BLOCKING.
+ */
+#define LABS_STATIC_MAX_REPLICAS 4096
+int32_t labs_mts_run_static(const labs_params* P, uint64_t seed, uint64_t first_instance,
+                            int64_t replicas, labs_result* h_out, labs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,8 +37,9 @@ EXPORTED = [
     "labs_last_error", "labs_version", "labs_energy_batch", "labs_tabu_run",
     "labs_mts_launch", "labs_mts_run", "labs_autotune", "labs_batch_create", "labs_batch_launch",
     "labs_batch_device_results", "labs_batch_results", "labs_batch_get_mapping",
-    "labs_batch_destroy", "labs_mts_batch_run",
+    "labs_batch_destroy", "labs_mts_batch_run", "labs_mts_run_static",
 ]
+STATIC_MAX_REPLICAS = 4096
 ORDER_LPT = 0
 ORDER_GIVEN = 1
 
@@ -177,6 +178,8 @@ def load(path: str = LIB_PATH):
         L.labs_batch_destroy.argtypes = [vp]
         L.labs_mts_batch_run.restype = i32
         L.labs_mts_batch_run.argtypes = [IP, i64, MP, RP, vp]
+        L.labs_mts_run_static.restype = i32
+        L.labs_mts_run_static.argtypes = [ctypes.POINTER(Params), u64, u64, i64, RP, vp]
         _lib = L
         return L
 
