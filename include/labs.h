@@ -264,6 +264,61 @@ int32_t labs_mts_batch_run(const labs_instance* h_inst, int64_t n, const labs_ma
                            labs_result* h_out, labs_stream_t stream);
 
 /*
+ * Solve service: continuous batching of solve requests on one GPU.
+ *
+ * A server owns a device arena of `max_slots` slots.  A scheduler thread
+ * admits pending requests (FIFO) into free slots as slots and memory free
+ * up -- a request is admitted when a slot is free, its population fits the
+ * HBM budget and its shared-memory footprint fits the quantum kernel -- and
+ * runs quanta: one bounded launch in which every admitted request advances
+ * by whole generations up to `quantum_steps` tabu steps, its population
+ * staying in device memory between quanta.  Requests that arrive while a
+ * quantum runs join at the next quantum.  A request's result is the same
+ * alone, in any mix, under any quantum size (it is the labs_mts_launch run
+ * of its instance).  Results carry the request's latency (submit -> result)
+ * in labs_result.seconds.
+ */
+typedef struct labs_serve_opts {
+    int32_t max_slots;          /* requests resident on the GPU at once (one warp each) */
+    int32_t max_N;              /* largest N accepted, 3 .. LABS_MAX_N */
+    int32_t max_K;              /* largest K accepted, 1 .. LABS_MAX_K */
+    int32_t warps_per_block;    /* quantum kernel CTA size in warps: 1, 2, 4 or 8 */
+    int64_t quantum_steps;      /* tabu steps per slot per quantum (rounded up to a generation) */
+    int64_t queue_capacity;     /* pending requests; submit answers LABS_EBUSY beyond it */
+    int64_t hbm_budget_bytes;   /* cap on the populations resident at once; 0: no cap */
+    int64_t quantum_timeout_ms; /* longest wait for one quantum before the server fails with
+                                   LABS_ETIMEOUT; 0: 60000 */
+} labs_serve_opts;
+
+/* One solve request: an MTS instance; max_steps or max_generations must bound it. */
+typedef labs_instance labs_request;
+
+typedef struct labs_serve_stats {
+    int64_t submitted, completed, canceled, quanta;
+    int64_t running, pending;
+    int64_t flip_evals;         /* tabu steps x N of every quantum so far */
+    double gpu_seconds;         /* summed quantum durations */
+    int32_t failed;             /* LABS_OK or the error that stopped the server */
+    int32_t pad;
+} labs_serve_stats;
+
+typedef struct labs_server labs_server; /* opaque */
+
+/* Creates a server (allocates its arena and starts its scheduler thread) on
+ * the current device; NULL on failure (see labs_last_error()). */
+labs_server* labs_serve_create(const labs_serve_opts* opts);
+/* Queues a request; *ticket identifies it.  LABS_EBUSY when the queue is full. */
+int32_t labs_serve_submit(labs_server* s, const labs_request* req, uint64_t* ticket);
+/* LABS_OK with the result (the ticket is then released), LABS_ENOTREADY,
+ * LABS_ECANCELED (released), LABS_ENOTFOUND, or the server's failure code. */
+int32_t labs_serve_poll(labs_server* s, uint64_t ticket, labs_result* out);
+/* Cancels a pending or running request (it leaves the GPU at the next quantum). */
+int32_t labs_serve_cancel(labs_server* s, uint64_t ticket);
+int32_t labs_serve_stats_get(labs_server* s, labs_serve_stats* out);
+/* Stops the scheduler, waits for the quantum in flight and frees everything. */
+int32_t labs_serve_destroy(labs_server* s);
+
+/*
  * labs_mts_run_static -- labs_mts_run without any memory allocation (no
  * counterpart in the paper; an interface for callers that cannot allocate).
  * Some callers may not allocate device memory at all: an application that

@@ -14,6 +14,7 @@ from __future__ import annotations
 from .api import (  # noqa: F401
     P_COMB_U32,
     Batch,
+    Server,
     autotune,
     make_instance,
     mts_batch_run,

@@ -37,7 +37,9 @@ EXPORTED = [
     "labs_last_error", "labs_version", "labs_energy_batch", "labs_tabu_run",
     "labs_mts_launch", "labs_mts_run", "labs_autotune", "labs_batch_create", "labs_batch_launch",
     "labs_batch_device_results", "labs_batch_results", "labs_batch_get_mapping",
-    "labs_batch_destroy", "labs_mts_batch_run", "labs_mts_run_static",
+    "labs_batch_destroy", "labs_mts_batch_run", "labs_mts_run_static", "labs_serve_create",
+    "labs_serve_submit", "labs_serve_poll", "labs_serve_cancel", "labs_serve_stats_get",
+    "labs_serve_destroy",
 ]
 STATIC_MAX_REPLICAS = 4096
 ORDER_LPT = 0
@@ -130,6 +132,34 @@ class Mapping(ctypes.Structure):
     ]
 
 
+class ServeOpts(ctypes.Structure):
+    _fields_ = [
+        ("max_slots", ctypes.c_int32),
+        ("max_N", ctypes.c_int32),
+        ("max_K", ctypes.c_int32),
+        ("warps_per_block", ctypes.c_int32),
+        ("quantum_steps", ctypes.c_int64),
+        ("queue_capacity", ctypes.c_int64),
+        ("hbm_budget_bytes", ctypes.c_int64),
+        ("quantum_timeout_ms", ctypes.c_int64),
+    ]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64),
+        ("completed", ctypes.c_int64),
+        ("canceled", ctypes.c_int64),
+        ("quanta", ctypes.c_int64),
+        ("running", ctypes.c_int64),
+        ("pending", ctypes.c_int64),
+        ("flip_evals", ctypes.c_int64),
+        ("gpu_seconds", ctypes.c_double),
+        ("failed", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+    ]
+
+
 assert ctypes.sizeof(DeviceResult) == 64
 assert ctypes.sizeof(Instance) == 64
 
@@ -178,6 +208,18 @@ def load(path: str = LIB_PATH):
         L.labs_batch_destroy.argtypes = [vp]
         L.labs_mts_batch_run.restype = i32
         L.labs_mts_batch_run.argtypes = [IP, i64, MP, RP, vp]
+        L.labs_serve_create.restype = vp
+        L.labs_serve_create.argtypes = [ctypes.POINTER(ServeOpts)]
+        L.labs_serve_submit.restype = i32
+        L.labs_serve_submit.argtypes = [vp, IP, ctypes.POINTER(u64)]
+        L.labs_serve_poll.restype = i32
+        L.labs_serve_poll.argtypes = [vp, u64, RP]
+        L.labs_serve_cancel.restype = i32
+        L.labs_serve_cancel.argtypes = [vp, u64]
+        L.labs_serve_stats_get.restype = i32
+        L.labs_serve_stats_get.argtypes = [vp, ctypes.POINTER(ServeStats)]
+        L.labs_serve_destroy.restype = i32
+        L.labs_serve_destroy.argtypes = [vp]
         L.labs_mts_run_static.restype = i32
         L.labs_mts_run_static.argtypes = [ctypes.POINTER(Params), u64, u64, i64, RP, vp]
         _lib = L

@@ -229,3 +229,62 @@ def mts_batch_run(instances, mapping=None, stream=None) -> list[dict]:
     nat.check(nat.load().labs_mts_batch_run(arr, n, ctypes.byref(m) if m is not None else None, res,
                                             _stream(stream)))
     return _result_dicts(res, n)
+
+
+# ---------------------------------------------------------------- serving
+
+
+class Server:
+    """Continuous-batching solve service (labs_serve_*): submit requests at any
+    time, poll for results; the library's scheduler thread runs the GPU."""
+
+    def __init__(self, max_slots: int = 1024, max_N: int = 256, max_K: int = 128,
+                 warps_per_block: int = 4, quantum_steps: int = 2000,
+                 queue_capacity: int = 1 << 20, hbm_budget_bytes: int = 0,
+                 quantum_timeout_ms: int = 0):
+        opts = nat.ServeOpts(max_slots, max_N, max_K, warps_per_block, quantum_steps,
+                             queue_capacity, hbm_budget_bytes, quantum_timeout_ms)
+        L = nat.load()
+        self._h = L.labs_serve_create(ctypes.byref(opts))
+        if not self._h:
+            msg = L.labs_last_error()
+            raise nat.LabsError(nat.LABS_EINVAL, msg.decode() if msg else "labs_serve_create failed")
+
+    def submit(self, instance: nat.Instance) -> int:
+        t = ctypes.c_uint64()
+        nat.check(nat.load().labs_serve_submit(self._h, ctypes.byref(instance), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int) -> dict | None:
+        """The result dict, or None while it is not ready."""
+        r = nat.Result()
+        rc = nat.load().labs_serve_poll(self._h, ticket, ctypes.byref(r))
+        if rc == nat.LABS_ENOTREADY:
+            return None
+        nat.check(rc)
+        return _result_dicts([r], 1)[0]
+
+    def cancel(self, ticket: int) -> None:
+        nat.check(nat.load().labs_serve_cancel(self._h, ticket))
+
+    def stats(self) -> dict:
+        st = nat.ServeStats()
+        nat.check(nat.load().labs_serve_stats_get(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in nat.ServeStats._fields_ if k != "pad"}
+
+    def close(self) -> None:
+        if self._h:
+            nat.load().labs_serve_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -50,7 +50,33 @@ struct BatchArgs {
     size_t smem_per_warp;
 };
 
+// Device record of one serving slot, between quanta.
+constexpr int32_t kSlotFresh = 0;      // admitted, population not built yet
+constexpr int32_t kSlotSuspended = 1;  // between two generations
+constexpr int32_t kSlotDone = 2;
+struct ServeState {
+    uint32_t best[2 * LABS_MAX_W];
+    int32_t E_best, status;
+    int64_t g, steps;
+    int32_t phase, pad[3];
+};
+
+struct ServeArgs {
+    const labs_instance* cfg;    // per slot
+    ServeState* state;           // per slot
+    uint32_t* pop;               // per-slot arena: K*NW words then K energies
+    size_t pop_stride_words;
+    const int32_t* active;       // slot of each active index
+    int32_t n_active;
+    int64_t quantum_steps;       // a slot stops at the first generation boundary past this
+    labs_device_result* out;     // per active index (finished slots only)
+    int32_t* done;               // per active index
+    int64_t* quantum_used;       // steps each active slot took in this quantum
+    size_t smem_per_warp;
+};
+
 size_t mts_smem_per_warp(int N, int K);
+cudaError_t launch_serve_quantum(const ServeArgs& a, int nwmax, int warps_per_block, cudaStream_t stream);
 cudaError_t batch_prepare(int nwmax, int warps_per_block, size_t smem_per_warp, int* max_blocks_per_sm);
 cudaError_t launch_batch(const BatchArgs& a, int nwmax, int blocks, int warps_per_block,
                          cudaStream_t stream);

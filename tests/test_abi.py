@@ -106,3 +106,15 @@ def test_batch_argument_errors_without_gpu(lib):
     arr[1].max_steps = 10
     assert lib.labs_batch_create(arr, 2, ctypes.byref(bad_map), None, ctypes.byref(h)) == nat.LABS_EINVAL
     assert lib.labs_batch_destroy(None) == nat.LABS_OK
+
+
+def test_serve_argument_errors_without_gpu(lib):
+    from paper_2504_00987_gb300 import _native as nat
+
+    bad = nat.ServeOpts(0, 64, 100, 4, 1000, 10, 0, 0)
+    assert not lib.labs_serve_create(ctypes.byref(bad))
+    assert b"max_slots" in lib.labs_last_error()
+    bad = nat.ServeOpts(16, 64, 100, 3, 1000, 10, 0, 0)
+    assert not lib.labs_serve_create(ctypes.byref(bad))
+    assert lib.labs_serve_destroy(None) == nat.LABS_OK
+    assert lib.labs_serve_poll(None, 1, None) == nat.LABS_EINVAL
