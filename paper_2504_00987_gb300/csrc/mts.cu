@@ -11,7 +11,7 @@
 
 namespace lgpu {
 
-template <int NW>
+template <int NW, bool TRACE>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) mts_kernel(const MtsArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -35,10 +35,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) mts_kernel(const MtsArgs 
     cfg.inst = static_cast<uint32_t>(a.first_instance + static_cast<uint64_t>(r));
     cfg.key = philox_key(a.seed);
     int4* trace = a.d_trace ? a.d_trace + r * a.trace_cap : nullptr;
-    replica_run<NW>(cfg, pop, popE, Cs, trace, a.trace_cap, a.d_glf, a.d_out + r, lane);
+    replica_run<NW, TRACE>(cfg, pop, popE, Cs, trace, a.trace_cap, a.d_glf, a.d_out + r, lane);
 }
 
-template <int NW>
+template <int NW, bool TRACE>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) tabu_kernel(const TabuArgs a) {
     __shared__ int32_t Cs_all[kWarpsPerBlock][32 * NW];
     const int lane = threadIdx.x & 31;
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) tabu_kernel(const TabuArg
     }
     int4* trace = a.d_trace ? a.d_trace + b * a.trace_cap : nullptr;
     int64_t trace_len = 0;
-    const TabuOut to = tabu_search<NW>(seq, N, key, inst, a.generation, max_iter, -1,
+    const TabuOut to = tabu_search<NW, TRACE>(seq, N, key, inst, a.generation, max_iter, -1,
                                        Cs_all[warp], trace, a.trace_cap, trace_len, lane);
     if (lane < NW) {
         uint32_t v = 0;
@@ -79,15 +79,20 @@ size_t mts_smem_per_warp(int N, int K) {
     return (bytes + 15) & ~static_cast<size_t>(15);
 }
 
-template <int NW>
-static cudaError_t launch_mts_w(const MtsArgs& a, cudaStream_t stream) {
+template <int NW, bool TRACE>
+static cudaError_t launch_mts_t(const MtsArgs& a, cudaStream_t stream) {
     const size_t smem = a.smem_per_warp * kWarpsPerBlock;
-    cudaError_t e = cudaFuncSetAttribute(mts_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(mts_kernel<NW, TRACE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     const int64_t blocks = (a.replicas + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    mts_kernel<NW><<<static_cast<unsigned>(blocks), kWarpsPerBlock * 32, smem, stream>>>(a);
+    mts_kernel<NW, TRACE><<<static_cast<unsigned>(blocks), kWarpsPerBlock * 32, smem, stream>>>(a);
     return cudaGetLastError();
+}
+
+template <int NW>
+static cudaError_t launch_mts_w(const MtsArgs& a, cudaStream_t stream) {
+    return a.d_trace ? launch_mts_t<NW, true>(a, stream) : launch_mts_t<NW, false>(a, stream);
 }
 
 cudaError_t launch_mts(const MtsArgs& a, cudaStream_t stream) {
@@ -102,7 +107,10 @@ cudaError_t launch_mts(const MtsArgs& a, cudaStream_t stream) {
 template <int NW>
 static cudaError_t launch_tabu_w(const TabuArgs& a, cudaStream_t stream) {
     const int64_t blocks = (a.B + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    tabu_kernel<NW><<<static_cast<unsigned>(blocks), kWarpsPerBlock * 32, 0, stream>>>(a);
+    if (a.d_trace)
+        tabu_kernel<NW, true><<<static_cast<unsigned>(blocks), kWarpsPerBlock * 32, 0, stream>>>(a);
+    else
+        tabu_kernel<NW, false><<<static_cast<unsigned>(blocks), kWarpsPerBlock * 32, 0, stream>>>(a);
     return cudaGetLastError();
 }
 

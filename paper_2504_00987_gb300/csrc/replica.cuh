@@ -112,7 +112,7 @@ __device__ __forceinline__ bool replica_should_stop(const ReplicaCfg& a, Replica
 }
 
 // One generation g = st.g.  Returns the tabu steps it took.
-template <int NW>
+template <int NW, bool TRACE = false>
 __device__ int64_t replica_generation(const ReplicaCfg& a, ReplicaState<NW>& st,
                                       uint32_t* __restrict__ pop, int32_t* __restrict__ popE,
                                       int32_t* __restrict__ Cs, int4* __restrict__ trace,
@@ -162,7 +162,7 @@ __device__ int64_t replica_generation(const ReplicaCfg& a, ReplicaState<NW>& st,
     // child <- Tabu-Search(child)
     const int max_iter = a.max_iter >= 0 ? a.max_iter : N / 2 + rand_int(0, N, uiter);
     const int64_t budget = a.max_steps >= 0 ? a.max_steps - st.steps : -1;
-    const TabuOut to = tabu_search<NW>(child, N, a.key, a.inst, gg, max_iter, budget, Cs, trace,
+    const TabuOut to = tabu_search<NW, TRACE>(child, N, a.key, a.inst, gg, max_iter, budget, Cs, trace,
                                        trace_cap, trace_len, lane);
     st.steps += to.steps;
     if (to.E_best < st.E_best) {
@@ -190,9 +190,11 @@ __device__ int64_t replica_generation(const ReplicaCfg& a, ReplicaState<NW>& st,
     store_seq<NW>(pop + slot * NW, child, lane);
     if (lane == 0) popE[slot] = to.E_best;
     __syncwarp();
-    if (trace != nullptr && trace_len < trace_cap) {
-        if (lane == 0) trace[trace_len] = make_int4(static_cast<int>(st.g), 0, slot, to.E_best);
-        ++trace_len;
+    if constexpr (TRACE) {
+        if (trace_len < trace_cap) {
+            if (lane == 0) trace[trace_len] = make_int4(static_cast<int>(st.g), 0, slot, to.E_best);
+            ++trace_len;
+        }
     }
     ++st.g;
     if (glf != nullptr && a.target_E >= 0 && to.E_best <= a.target_E && lane == 0) atomicExch(glf, 1u);
@@ -218,7 +220,7 @@ __device__ __forceinline__ void replica_store_result(const ReplicaState<NW>& st,
 }
 
 // A whole replica from scratch to its stop condition.
-template <int NW>
+template <int NW, bool TRACE = false>
 __device__ __forceinline__ void replica_run(const ReplicaCfg& a, uint32_t* pop, int32_t* popE,
                                             int32_t* Cs, int4* trace, int64_t trace_cap,
                                             uint32_t* glf, labs_device_result* out, int lane) {
@@ -226,7 +228,7 @@ __device__ __forceinline__ void replica_run(const ReplicaCfg& a, uint32_t* pop, 
     int64_t trace_len = 0;
     replica_init<NW>(a, pop, popE, st, lane);
     while (!replica_should_stop<NW>(a, st, glf))
-        replica_generation<NW>(a, st, pop, popE, Cs, trace, trace_cap, trace_len, glf, lane);
+        replica_generation<NW, TRACE>(a, st, pop, popE, Cs, trace, trace_cap, trace_len, glf, lane);
     replica_store_result<NW>(st, trace_len, out, lane);
 }
 

@@ -147,30 +147,17 @@ __device__ __forceinline__ void score_planes(const int32_t (&c)[NW], const uint3
     }
 }
 
-// T_j = PC(j) + PC(N-1-j) = Total + sum_{i=1}^{j} (C_i - C_{N-i}) for the
-// lane's j = lane + 32q.  Two chunks are scanned together in one 32-bit
-// value (low and high 16-bit halves): every within-chunk prefix is bounded
-// by 32 * 2 * (N-1) < 2^15.
+// Inclusive prefix sums of C at the lane's own indices: pc[q] = PC(l + 32q),
+// PC(n) = sum_{k=1}^{n} C_k (C_0 = 0).  Two chunks share one packed 32-bit
+// shuffle scan (low and high 16-bit halves; every within-chunk prefix is
+// bounded by 32 (N-1) < 2^15).  Used once per search; afterwards the sums
+// are updated incrementally per move.
 template <int NW>
-__device__ __forceinline__ void prefix_terms(const int32_t (&c)[NW], int N, int lane,
-                                             int32_t* __restrict__ Cs, int32_t (&T)[NW]) {
-#pragma unroll
-    for (int q = 0; q < NW; ++q) Cs[lane + 32 * q] = c[q];
-    __syncwarp();
-    int32_t tot = 0;
-    int32_t D[NW];
-#pragma unroll
-    for (int q = 0; q < NW; ++q) {
-        const int i = lane + 32 * q;
-        const bool in = i >= 1 && i <= N - 1;
-        D[q] = in ? c[q] - Cs[in ? N - i : 0] : 0;
-        tot += c[q];
-    }
-    __syncwarp();
-    int32_t carry = __reduce_add_sync(kFull, tot);
+__device__ __forceinline__ void prefix_own(const int32_t (&c)[NW], int lane, int32_t (&pc)[NW]) {
+    int32_t carry = 0;
 #pragma unroll
     for (int q = 0; q < NW; q += 2) {
-        int32_t v = D[q] + D[q + 1] * 65536;
+        int32_t v = c[q] + c[q + 1] * 65536;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int32_t n = __shfl_up_sync(kFull, v, o);
@@ -181,46 +168,44 @@ __device__ __forceinline__ void prefix_terms(const int32_t (&c)[NW], int N, int 
         const int32_t hi = (v - lo) / 65536;
         const int32_t lo31 = static_cast<int32_t>(static_cast<int16_t>(last & 0xFFFF));
         const int32_t hi31 = (last - lo31) / 65536;
-        T[q] = carry + lo;
-        T[q + 1] = carry + lo31 + hi;
+        pc[q] = carry + lo;
+        pc[q + 1] = carry + lo31 + hi;
         carry += lo31 + hi31;
     }
 }
 
-// Scores every neighbour of the pivot: S_j on P bit planes and T_j from the
-// packed scan, in one block so the two independent chains overlap.
-template <int NW, int P>
-__device__ __forceinline__ void score_all(const int32_t (&c)[NW], const uint32_t (&par)[NW],
-                                          const uint32_t (&X)[NW][NW], const uint32_t (&Y)[NW][NW],
-                                          int N, int lane, int32_t* __restrict__ Cs,
-                                          int32_t (&S)[NW], int32_t (&T)[NW]) {
+// T_j = PC(j) + PC(N-1-j) for the lane's j = l + 32q: its own prefix plus
+// the mirror index's prefix, read back through the warp's shared scratch.
+template <int NW>
+__device__ __forceinline__ void mirror_terms(const int32_t (&pc)[NW], int N, int lane,
+                                             int32_t* __restrict__ Cs, int32_t (&T)[NW]) {
 #pragma unroll
-    for (int q = 0; q < NW; ++q) S[q] = 0;
-    prefix_terms<NW>(c, N, lane, Cs, T);
-    score_planes<NW, P>(c, par, X, Y, S);
+    for (int q = 0; q < NW; ++q) Cs[lane + 32 * q] = pc[q];
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        const int j = lane + 32 * q;
+        T[q] = pc[q] + Cs[j < N ? N - 1 - j : 0];
+    }
+    __syncwarp();
 }
 
+// Scores S_j with P bit planes, where P >= the planes C_k needs (extra
+// planes only repeat the sign and leave the sum exact).  Three fully
+// unrolled widths keep the code small enough for the instruction cache
+// (a jump table over every width measured several hundred cycles slower).
 template <int NW>
-__device__ __forceinline__ void score_dispatch(int P, const int32_t (&c)[NW],
-                                               const uint32_t (&par)[NW],
-                                               const uint32_t (&X)[NW][NW],
-                                               const uint32_t (&Y)[NW][NW], int N, int lane,
-                                               int32_t* __restrict__ Cs, int32_t (&S)[NW],
-                                               int32_t (&T)[NW]) {
-    switch (P) {
-        case 2: score_all<NW, 2>(c, par, X, Y, N, lane, Cs, S, T); break;
-        case 3: score_all<NW, 3>(c, par, X, Y, N, lane, Cs, S, T); break;
-        case 4: score_all<NW, 4>(c, par, X, Y, N, lane, Cs, S, T); break;
-        case 5: score_all<NW, 5>(c, par, X, Y, N, lane, Cs, S, T); break;
-        case 6: score_all<NW, 6>(c, par, X, Y, N, lane, Cs, S, T); break;
-        case 7: score_all<NW, 7>(c, par, X, Y, N, lane, Cs, S, T); break;
-        case 8:
-            if constexpr (PlaneMax<NW>::value >= 8) score_all<NW, 8>(c, par, X, Y, N, lane, Cs, S, T);
-            break;
-        default:
-            if constexpr (PlaneMax<NW>::value >= 9) score_all<NW, 9>(c, par, X, Y, N, lane, Cs, S, T);
-            break;
-    }
+__device__ __forceinline__ void score_dispatch(int P, const int32_t (&c)[NW], const uint32_t (&par)[NW],
+                                               const uint32_t (&X)[NW][NW], const uint32_t (&Y)[NW][NW],
+                                               int32_t (&S)[NW]) {
+#pragma unroll
+    for (int q = 0; q < NW; ++q) S[q] = 0;
+    if (P <= 5)
+        score_planes<NW, 5>(c, par, X, Y, S);
+    else if (P <= 6)
+        score_planes<NW, 6>(c, par, X, Y, S);
+    else
+        score_planes<NW, PlaneMax<NW>::value>(c, par, X, Y, S);
 }
 
 // Number of two's-complement planes that hold every C_k of the warp:
@@ -235,15 +220,19 @@ __device__ __forceinline__ int plane_count(const int32_t (&c)[NW]) {
 
 // One tabu search from `seq` (warp-uniform).  On return `seq` holds
 // bestSeqTS.  Draws: step t uses Philox(instance, g, t, 4): x tie, y tenure.
-// `Cs` is warp-private shared scratch of 32*NW ints.  `trace` (nullable)
+// `Cs` is warp-private shared scratch of 32*NW ints.  With TRACE, `trace`
 // receives {g, t, j, E} per step while trace_len < trace_cap.
-template <int NW>
+template <int NW, bool TRACE>
 __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key,
                                const uint32_t inst, const uint32_t g, const int max_iter,
                                const int64_t budget, int32_t* __restrict__ Cs,
                                int4* __restrict__ trace, const int64_t trace_cap,
                                int64_t& trace_len, const int lane) {
     constexpr int NB = 32 * NW;
+    // Correlations are recomputed from the pivot after every move when the
+    // windows are short (cheaper on the ALU pipe than the per-k update),
+    // and updated incrementally otherwise.
+    constexpr bool kRecompute = NW <= 4;
     uint32_t B[NW], RL[NW], Bb[NW];
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
@@ -261,24 +250,29 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
         E = __reduce_add_sync(kFull, sq);
     }
     int32_t E_best = E;
-    int32_t tabu[NW];
-    // Per-search constants: parity plane (bit k set iff 1 <= k <= N-1 and
-    // N - k odd) and the masks of k in [1, min(j, N-1-j)] used by M_j.
+    // Per-search constants of the lane's neighbours j = lane + 32q: the
+    // parity plane of C_k (bit k set iff 1 <= k <= N-1 and N - k odd), the
+    // masks of k in [1, L_j] with L_j = min(j, N-1-j) used by M_j, L_j, and
+    // the mirror index N-1-j of T_j.
     uint32_t par[NW];
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
         const uint32_t alt = ((N - 32 * w) & 1) ? 0x55555555u : 0xAAAAAAAAu;  // (N - k) odd
         par[w] = alt & word_lowmask(w, N) & (w == 0 ? ~1u : kFull);
     }
+    int32_t tabu[NW], Lq[NW], mir[NW];
     uint32_t mmask[NW][NW];
+    uint32_t jvalid = 0;  // bit q: j < N
 #pragma unroll
     for (int q = 0; q < NW; ++q) {
         tabu[q] = 0;
         const int j = lane + 32 * q;
-        const int L = min(j, N - 1 - j);
+        Lq[q] = min(j, N - 1 - j);
+        mir[q] = j < N ? N - 1 - j : 0;
+        jvalid |= (j < N ? 1u : 0u) << q;
 #pragma unroll
         for (int w = 0; w <= q && w + q < NW; ++w)
-            mmask[q][w] = word_lowmask(w, L + 1) & (w == 0 ? ~1u : kFull);
+            mmask[q][w] = word_lowmask(w, Lq[q] + 1) & (w == 0 ? ~1u : kFull);
     }
     const int min_t = max_iter / 10;
     const int max_t = (12 * max_iter) / 100;
@@ -286,6 +280,15 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
     uint32_t rx = 0, ry = 0;
     int64_t steps = 0;
     int P = plane_count<NW>(c);
+    int32_t pc[NW], T[NW];
+    prefix_own<NW>(c, lane, pc);
+#pragma unroll
+    for (int q = 0; q < NW; ++q) Cs[lane + 32 * q] = pc[q];
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < NW; ++q) T[q] = pc[q] + Cs[mir[q]];
+    __syncwarp();
+    const uint32_t low_l = (lane == 31) ? kFull : ((2u << lane) - 1u);  // bits 0..lane
 
     for (int t = 1; t <= nsteps; ++t) {
         if (((t - 1) & 31) == 0) {  // draws of steps t .. t+31, one per lane
@@ -308,24 +311,23 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
                 Y[q][w] = __funnelshift_r(RL[w + NW - 1 - q], (w + NW - q < NW) ? RL[w + NW - q] : 0u,
                                           31 - lane);
         }
-        // ---- S_j on the bit planes of C_k; T_j from the packed scan
-        int32_t S[NW], T[NW];
-        score_dispatch<NW>(P, c, par, X, Y, N, lane, Cs, S, T);
+        // ---- S_j on the bit planes of C_k (T_j is kept up to date by the moves)
+        int32_t S[NW];
+        score_dispatch<NW>(P, c, par, X, Y, S);
         // ---- E_j, admissibility (tabu expired or aspiration), candidates
         const int32_t E0 = E + 4 * (N - 1);
         int32_t cand[NW];
         int32_t lmin = INT_MAX;
 #pragma unroll
         for (int q = 0; q < NW; ++q) {
-            const int j = lane + 32 * q;
             int dm = 0;
 #pragma unroll
             for (int w = 0; w <= q && w + q < NW; ++w) dm += __popc((X[q][w] ^ Y[q][w]) & mmask[q][w]);
-            const int L = min(j, N - 1 - j);
-            const int32_t M = L - 2 * dm;
-            const int32_t sj = ((B[q] >> lane) & 1u) ? 1 : -1;
-            const int32_t Ej = E0 + 8 * M - 4 * sj * (2 * S[q] - T[q]);
-            const bool adm = j < N && (tabu[q] < t || Ej < E_best);
+            const int32_t M = Lq[q] - 2 * dm;
+            const int32_t V = 2 * S[q] - T[q];
+            const int32_t sv = (X[q][0] & 1u) ? V : -V;  // s_j (2 S_j - T_j); bit 0 of X_j is b_j
+            const int32_t Ej = E0 + 8 * M - 4 * sv;
+            const bool adm = ((jvalid >> q) & 1u) && (tabu[q] < t || Ej < E_best);
             cand[q] = adm ? Ej : INT_MAX;
             lmin = min(lmin, cand[q]);
         }
@@ -338,43 +340,67 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
             tb[q] = __ballot_sync(kFull, cand[q] == m);
             count += __popc(tb[q]);
         }
-        int p = 0;
-        if (count == 1) {
+        // lowest admissible minimiser; it is the pick whenever the tie draw selects index 0
+        int lj = INT_MAX;
 #pragma unroll
-            for (int q = NW - 1; q >= 0; --q)
-                if (tb[q]) p = 32 * q + __ffs(tb[q]) - 1;
-        } else {
-            int idx = static_cast<int>((static_cast<uint64_t>(u_tie) * count) >> 32);
+        for (int q = NW - 1; q >= 0; --q)
+            if (cand[q] == m) lj = lane + 32 * q;
+        int p = __reduce_min_sync(kFull, lj);
+        int idx = count > 1 ? static_cast<int>((static_cast<uint64_t>(u_tie) * count) >> 32) : 0;
+        if (idx > 0) {
             bool found = false;
 #pragma unroll
             for (int q = 0; q < NW; ++q) {
-                const int pc = __popc(tb[q]);
+                const int pc_q = __popc(tb[q]);
                 if (!found) {
-                    if (idx < pc) {
+                    if (idx < pc_q) {
                         p = 32 * q + nth_set_bit(tb[q], idx);
                         found = true;
                     } else {
-                        idx -= pc;
+                        idx -= pc_q;
                     }
                 }
             }
         }
-        // ---- apply: C_k += delta_k(p), flip, tenure, bestSeqTS
+        // ---- apply: windows of the move, C_k, PC(n), flip, tenure, bestSeqTS
         uint32_t Xp[NW], Yp[NW];
         shr_uniform<NW>(B, p, Xp);            // bit k = b_{p+k}
         shr_uniform<NW>(RL, NB - 1 - p, Yp);  // bit k = b_{p-k}
         const int32_t sp2 = (Xp[0] & 1u) ? 2 : -2;
-#pragma unroll
-        for (int q = 0; q < NW; ++q) {
-            const int k = lane + 32 * q;
-            const int32_t bx = (Xp[q] >> lane) & 1u, by = (Yp[q] >> lane) & 1u;
-            const int32_t sx = (k >= 1 && k + p <= N - 1) ? 2 * bx - 1 : 0;
-            const int32_t sy = (k >= 1 && k <= p) ? 2 * by - 1 : 0;
-            c[q] -= sp2 * (sx + sy);
-        }
-        P = plane_count<NW>(c);  // for the next step; overlaps with the tail below
         flip_bit<NW>(B, p);
         flip_bit<NW>(RL, NB - 1 - p);
+        if constexpr (kRecompute) {
+            correlations<NW>(B, N, lane, c);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NW; ++q) {
+                const int k = lane + 32 * q;
+                const int32_t bx = (Xp[q] >> lane) & 1u, by = (Yp[q] >> lane) & 1u;
+                const int32_t sx = (k >= 1 && k + p <= N - 1) ? 2 * bx - 1 : 0;
+                const int32_t sy = (k >= 1 && k <= p) ? 2 * by - 1 : 0;
+                c[q] -= sp2 * (sx + sy);
+            }
+        }
+        P = plane_count<NW>(c);  // for the next step; overlaps with the tail below
+        // PC(n) += sum_{k=1}^{n} delta_k(p)
+        //       = -2 s_p [2 (#ones of b_{p+k}, b_{p-k} for k in 1..n) - min(n, N-1-p) - min(n, p)]
+        {
+            const int32_t bp = static_cast<int32_t>(Xp[0] & 1u);  // bit 0 of both windows is b_p
+            int32_t ux = 0;                                         // ones in whole words below q
+#pragma unroll
+            for (int q = 0; q < NW; ++q) {
+                const int n = lane + 32 * q;
+                const int32_t ones = ux + __popc(Xp[q] & low_l) + __popc(Yp[q] & low_l) - 2 * bp;
+                pc[q] -= sp2 * (2 * ones - min(n, N - 1 - p) - min(n, p));
+                if (q + 1 < NW) ux += __popc(Xp[q]) + __popc(Yp[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NW; ++q) Cs[lane + 32 * q] = pc[q];
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < NW; ++q) T[q] = pc[q] + Cs[mir[q]];
+        __syncwarp();
         const int32_t expiry = t + rand_int(min_t, max_t, u_ten);
 #pragma unroll
         for (int q = 0; q < NW; ++q)
@@ -386,9 +412,11 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
             for (int w = 0; w < NW; ++w) Bb[w] = B[w];
         }
         ++steps;
-        if (trace != nullptr && trace_len < trace_cap) {
-            if (lane == 0) trace[trace_len] = make_int4(static_cast<int>(g), t, p, m);
-            ++trace_len;
+        if constexpr (TRACE) {
+            if (trace_len < trace_cap) {
+                if (lane == 0) trace[trace_len] = make_int4(static_cast<int>(g), t, p, m);
+                ++trace_len;
+            }
         }
     }
 #pragma unroll
