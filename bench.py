@@ -27,6 +27,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2504_00987_gb300 import parallel  # noqa: E402  (host logic only; no CUDA at import)
+
 N, K, REPLICAS, STEPS_PER_REPLICA = 64, 100, 1024, 100_000
 WORKLOAD = "replicas_n64"
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
@@ -203,7 +205,7 @@ def run_gpu(args) -> None:
         REPLICAS = args.replicas
     if args.steps_per_replica:
         STEPS_PER_REPLICA = args.steps_per_replica
-    first = rank * REPLICAS
+    first, _ = parallel.shard(world, rank, REPLICAS)
     P = labs.make_params(N, K, max_steps=STEPS_PER_REPLICA)
     out = torch.empty((REPLICAS, 8), dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -248,13 +250,10 @@ def run_gpu(args) -> None:
     if not e2e_ms:
         e2e_ms = [float("nan")]
 
-    # max over ranks of the timed region
-    if pg is not None:
-        t = torch.tensor([local_ms, sum(e2e_ms) / len(e2e_ms)], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms, e2e_step_ms = float(t[0]), float(t[1])
-    else:
-        total_ms, e2e_step_ms = local_ms, sum(e2e_ms) / len(e2e_ms)
+    # max over ranks of the timed region; the best replica of the whole job
+    total_ms, e2e_step_ms = parallel.max_over_ranks(pg, [local_ms, sum(e2e_ms) / len(e2e_ms)], dev)
+    lbest = min(res, key=lambda r: (r["E"], r["instance"]))
+    best_E, best_inst = parallel.best_over_ranks(pg, lbest["E"], lbest["instance"], dev)
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
@@ -287,6 +286,7 @@ def run_gpu(args) -> None:
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": REPLICAS * 64,
                 "call": "labs_mts_run (blocking; results copied to host)"},
         "gpu_launches": args.steps,
+        "best_E": best_E, "best_merit_factor": N * N / (2.0 * best_E), "best_instance": best_inst,
         "wall_s_timed": wall,
         "clocks": clock,
     }
@@ -296,6 +296,269 @@ def run_gpu(args) -> None:
     print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------- other workloads
+# These print one JSON line each for the configurations beside the default
+# one: the N = 92..120 sweep, time-to-target, the uneven batch and the solve
+# service.  Each compares against the plain form where the contract names one.
+
+TARGETS_FILE = os.path.join(ROOT, "tests", "golden", "targets.json")
+
+
+def gpu_context(args):
+    import torch
+
+    from paper_2504_00987_gb300 import _build
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _build.build()
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    return torch, dev, pg, world, rank
+
+
+def load_targets(kind: str) -> dict:
+    with open(TARGETS_FILE) as f:
+        return {int(n): v["E"] for n, v in json.load(f)[kind]["targets"].items()}
+
+
+def timed_launch(torch, fn, stream):
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    out = fn()
+    e.record(stream)
+    e.synchronize()
+    return s.elapsed_time(e), out
+
+
+def run_sweep(args) -> None:
+    """N = 92, 96, ..., 120 (two words), one K=100 population per warp, 8 warps per SM."""
+    torch, dev, pg, world, rank = gpu_context(args)
+    import paper_2504_00987_gb300 as labs
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    reps = args.replicas or sms * 8
+    steps = args.steps_per_replica or 1_000_000
+    first, _ = parallel.shard(world, rank, reps)
+    stream = torch.cuda.current_stream()
+    rows, tot_flips, tot_ms = [], 0, 0.0
+    for n in range(92, 121, 4):
+        P = labs.make_params(n, 100, max_steps=steps)
+        warm = labs.make_params(n, 100, max_steps=max(1, steps // 100))
+        for _ in range(args.warmup):
+            labs.mts_launch(warm, 0, first, reps)
+        ms_list = []
+        for _ in range(args.steps):
+            ms, out = timed_launch(torch, lambda: labs.mts_launch(P, 0, first, reps, stream=stream), stream)
+            ms_list.append(ms)
+        ms = parallel.max_over_ranks(pg, [statistics.mean(ms_list)], dev)[0]
+        res = labs.decode_results(out, n, first)
+        lb = min(res, key=lambda r: (r["E"], r["instance"]))
+        bE, bi = parallel.best_over_ranks(pg, lb["E"], lb["instance"], dev)
+        flips = reps * steps * n * world
+        rows.append({"N": n, "ms": ms, "flip_evals_per_s": flips / (ms / 1e3),
+                     "pair_terms_per_s": flips * (n - 1) / (ms / 1e3), "best_E": bE,
+                     "best_merit_factor": n * n / (2.0 * bE), "best_instance": bi})
+        tot_flips += flips
+        tot_ms += ms
+    if rank == 0:
+        print(json.dumps({
+            "metric": "flip-evals/s", "value": tot_flips / (tot_ms / 1e3), "unit": "flip-evals/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"sweep_n92_120: N=92..120 step 4, K=100, {reps} replicas x {steps} steps per N",
+                       "replicas_per_gpu": reps, "steps_per_replica": steps},
+            "per_N": rows}), flush=True)
+
+
+def run_tts(args) -> None:
+    """Time to target E (the oracle's one-minute best, tests/golden/targets.json) with every
+    replica of the launch stopped by the global termination flag; p50/p99 over runs with
+    distinct seeds."""
+    torch, dev, pg, world, rank = gpu_context(args)
+    import numpy as np
+
+    import paper_2504_00987_gb300 as labs
+
+    targets = load_targets("sweep_n92_120")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    reps = args.replicas or sms * 8
+    cap = args.steps_per_replica or 10_000_000
+    runs = args.runs
+    stream = torch.cuda.current_stream()
+    Ns = [int(x) for x in args.tts_n.split(",")] if args.tts_n else sorted(targets)
+    rows = []
+    for n in Ns:
+        target = targets[n]
+        P = labs.make_params(n, 100, target_E=target, max_steps=cap, glf=True)
+        labs.mts_launch(labs.make_params(n, 100, max_steps=1000), 0, 0, reps)
+        times, reached = [], 0
+        for run in range(runs):
+            flag = torch.zeros(1, dtype=torch.int32, device=dev)
+            ms, out = timed_launch(torch, lambda: labs.mts_launch(P, 1000 + run, 0, reps, glf_flag=flag,
+                                                                  stream=stream), stream)
+            res = labs.decode_results(out, n)
+            ok = any(r["status"] == labs.RUN_REACHED for r in res)
+            reached += ok
+            times.append(ms / 1e3 if ok else float("inf"))
+        t = np.array(times)
+        rows.append({"N": n, "target_E": target, "runs": runs, "reached": reached,
+                     "p50_s": float(np.percentile(t, 50)), "p99_s": float(np.percentile(t, 99)),
+                     "q1_s": float(np.percentile(t, 25)), "q3_s": float(np.percentile(t, 75))})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "time-to-target-E p50", "value": statistics.median(r["p50_s"] for r in rows),
+            "unit": "s", "n_gpus": world, "higher_is_better": False, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"tts_n92_120: {reps} replicas with the global termination flag, K=100, "
+                                   f"cap {cap} steps, target = oracle one-minute best", "runs_per_N": runs},
+            "per_N": rows}), flush=True)
+
+
+def run_batch(args) -> None:
+    """512 uneven instances (N ~ U{40..127}, K ~ U{50..200}, 10 N^2 steps) in one autotuned,
+    graph-captured persistent launch vs one launch per instance."""
+    torch, dev, pg, world, rank = gpu_context(args)
+    import paper_2504_00987_gb300 as labs
+    from paper_2504_00987_gb300 import workloads
+
+    wl = workloads.uneven_batch(512, seed=7, steps_per_n2=10)
+    lo, cnt = parallel.split_range(len(wl), world, rank)
+    wl = wl[lo:lo + cnt]
+    inst = [labs.make_instance(x.N, x.K, seed=x.seed, instance=x.instance, max_steps=x.max_steps) for x in wl]
+    flips = sum(x.max_steps * x.N for x in wl)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    mapping = labs.autotune(inst)
+    tune_s = time.perf_counter() - t0
+    with labs.Batch(inst, mapping=mapping) as b:
+        for _ in range(args.warmup):
+            b.launch()
+        torch.cuda.synchronize()
+        ms_list = [timed_launch(torch, lambda: b.launch(stream), stream)[0] for _ in range(args.steps)]
+    ms = parallel.max_over_ranks(pg, [statistics.mean(ms_list)], dev)[0]
+    total_flips = parallel.sum_over_ranks(pg, [float(flips)], dev)[0]
+    # plain form: one launch per instance, back to back, on every 16th instance
+    sample = wl[::16]
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for x in sample:
+        labs.mts_launch(labs.make_params(x.N, x.K, max_steps=x.max_steps), x.seed, x.instance, 1)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t1
+    plain_rate = sum(x.max_steps * x.N for x in sample) / plain_s
+    if rank == 0:
+        value = total_flips / (ms / 1e3)
+        print(json.dumps({
+            "metric": "flip-evals/s", "value": value, "unit": "flip-evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong", "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "batch_uneven_512: N~U{40..127}, K~U{50..200}, 10 N^2 steps, seed 7",
+                       "mapping": mapping, "autotune_s": tune_s},
+            "plain_one_launch_per_instance": {"flip_evals_per_s": plain_rate, "sample": len(sample)},
+            "speedup_vs_plain": value / plain_rate}), flush=True)
+
+
+def run_serve(args) -> None:
+    """Poisson solve requests (mean 200/s, N ~ U{32..160}, K=100, half with a target E = the
+    oracle's ten-second best, half capped at 10^5 steps) through the continuous-batching
+    service, and the same stream as one launch per request on a pool of streams."""
+    torch, dev, pg, world, rank = gpu_context(args)
+    import numpy as np
+
+    import paper_2504_00987_gb300 as labs
+    from paper_2504_00987_gb300 import workloads
+
+    targets = load_targets("serve_n32_160")
+    reqs = workloads.poisson_requests(args.requests, 200.0, seed=11)
+    lo, cnt = parallel.split_range(len(reqs), world, rank)
+    reqs = reqs[lo:lo + cnt]
+
+    def instance(i, r):
+        if r.target_mode:
+            return labs.make_instance(r.N, r.K, seed=11, instance=lo + i, target_E=targets[r.N],
+                                      max_steps=r.max_steps)
+        return labs.make_instance(r.N, r.K, seed=11, instance=lo + i, max_steps=r.max_steps)
+
+    insts = [instance(i, r) for i, r in enumerate(reqs)]
+
+    def drive(submit, poll):
+        done, pending, i = {}, [], 0
+        t0 = time.perf_counter()
+        while len(done) < len(reqs):
+            now = time.perf_counter() - t0
+            while i < len(reqs) and reqs[i].arrival_s <= now:
+                pending.append((i, submit(i), t0 + reqs[i].arrival_s))
+                i += 1
+            keep = []
+            for k, h, t_arr in pending:
+                res = poll(h)
+                if res is None:
+                    keep.append((k, h, t_arr))
+                else:
+                    done[k] = (res, time.perf_counter() - t_arr)
+            pending = keep
+            time.sleep(0.0002)
+        return done, time.perf_counter() - t0
+
+    with labs.Server(max_slots=args.slots or 4096, max_N=160, max_K=100, quantum_steps=2000) as srv:
+        done, wall = drive(lambda i: srv.submit(insts[i]), srv.poll)
+        st = srv.stats()
+    lat = np.array([done[k][1] for k in range(len(reqs))])
+    tmode = np.array([r.target_mode for r in reqs])
+    missed = sum(1 for k, r in enumerate(reqs) if r.target_mode and done[k][0]["status"] != labs.RUN_REACHED)
+    served_rate = st["flip_evals"] / wall
+    # one launch per request, 64 streams round robin, on a prefix of the same stream
+    nb = min(len(reqs), args.baseline_requests)
+    streams = [torch.cuda.Stream() for _ in range(64)]
+    outs, evs = {}, {}
+
+    def submit_plain(i):
+        x = insts[i]
+        st_ = streams[i % len(streams)]
+        P = labs.make_params(x.N, x.K, max_steps=x.max_steps, target_E=x.target_E)
+        outs[i] = labs.mts_launch(P, x.seed, x.instance, 1, stream=st_)
+        ev = torch.cuda.Event()
+        ev.record(st_)
+        evs[i] = ev
+        return i
+
+    def poll_plain(i):
+        return {"done": True} if evs[i].query() else None
+
+    saved = reqs
+    reqs = reqs[:nb]
+    done_b, wall_b = drive(submit_plain, poll_plain)
+    reqs = saved
+    lat_b = np.array([done_b[k][1] for k in range(nb)])
+    flips_b = sum(labs.decode_results(outs[k], insts[k].N)[0]["flip_evals"] for k in range(nb))
+    if rank == 0:
+        print(json.dumps({
+            "metric": "flip-evals/s", "value": served_rate, "unit": "flip-evals/s", "n_gpus": world,
+            "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"serve_poisson: {args.requests} requests at 200/s, N~U{{32..160}}, K=100, "
+                                   "half target mode (oracle 10 s best, cap 1e7 steps), half 1e5 steps, seed 11",
+                       "slots": args.slots or 4096, "quantum_steps": 2000},
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "p50_target_mode": float(np.percentile(lat[tmode], 50)) if tmode.any() else None,
+                          "p99_target_mode": float(np.percentile(lat[tmode], 99)) if tmode.any() else None,
+                          "p50_cap_mode": float(np.percentile(lat[~tmode], 50)) if (~tmode).any() else None,
+                          "p99_cap_mode": float(np.percentile(lat[~tmode], 99)) if (~tmode).any() else None},
+            "target_misses": missed, "wall_s": wall, "gpu_busy_s": st["gpu_seconds"], "quanta": st["quanta"],
+            "plain_one_launch_per_request": {
+                "requests": nb, "flip_evals_per_s": flips_b / wall_b,
+                "latency_p50_s": float(np.percentile(lat_b, 50)),
+                "latency_p99_s": float(np.percentile(lat_b, 99))},
+        }), flush=True)
 
 
 def main() -> None:
@@ -308,11 +571,26 @@ def main() -> None:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--replicas", type=int, default=0, help="profiling only: override replicas")
     ap.add_argument("--steps-per-replica", type=int, default=0, help="profiling only: override budget")
+    ap.add_argument("--workload", choices=["replicas_n64", "sweep_n92_120", "tts", "batch", "serve"],
+                    default="replicas_n64")
+    ap.add_argument("--runs", type=int, default=50, help="tts: runs per N")
+    ap.add_argument("--tts-n", default="", help="tts: comma-separated N (default: all)")
+    ap.add_argument("--requests", type=int, default=20_000, help="serve: requests")
+    ap.add_argument("--baseline-requests", type=int, default=400, help="serve: plain-form prefix")
+    ap.add_argument("--slots", type=int, default=0, help="serve: resident slots")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "sweep_n92_120":
+        run_sweep(args)
+    elif args.workload == "tts":
+        run_tts(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

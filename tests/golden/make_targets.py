@@ -1,0 +1,77 @@
+"""Writes tests/golden/targets.json: target energies for the time-to-target
+measurements, computed by the CPU oracle only.
+
+Two sets, each a fixed amount of oracle work so the file is reproducible
+(step budgets instead of wall-clock limits):
+
+  sweep_n92_120 -- for N = 92, 96, ..., 120: the best E of 8 oracle replicas
+                   (seed 0, instances 0..7), each with 7.2e5 * (120/N)^2 tabu
+                   steps, about one minute of the incremental oracle on 8
+                   cores of a current x86 host ("the oracle's 60 s best").
+  serve_n32_160 -- for N = 32..160: the best E of one oracle replica (seed 0,
+                   instance 0) with 4.3e5 * (64/N)^2 steps, about ten seconds
+                   of one core ("the oracle's 10 s best").
+
+Usage:  python tests/golden/make_targets.py [--only sweep|serve] [--threads T]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import oracle  # noqa: E402
+
+OUT = os.path.join(HERE, "targets.json")
+
+
+def sweep_steps(N: int) -> int:
+    return int(7.2e5 * (120 / N) ** 2)
+
+
+def serve_steps(N: int) -> int:
+    return int(4.3e5 * (64 / N) ** 2)
+
+
+def run_one(N: int, instance: int, steps: int) -> int:
+    P = oracle.make_params(N, 100, max_steps=steps)
+    return oracle.mts_run(P, 0, instance)[0]["E"]
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--only", choices=["sweep", "serve"], default=None)
+    ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
+    args = ap.parse_args()
+    oracle.build()
+    data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    t0 = time.time()
+    with ThreadPoolExecutor(max_workers=args.threads) as ex:
+        if args.only in (None, "sweep"):
+            sweep = {}
+            for N in range(92, 121, 4):
+                Es = list(ex.map(lambda i, N=N: run_one(N, i, sweep_steps(N)), range(8)))
+                sweep[str(N)] = {"E": min(Es), "replicas": 8, "steps_per_replica": sweep_steps(N)}
+                print(f"sweep N={N}: E={min(Es)}  ({time.time() - t0:.0f}s)", flush=True)
+            data["sweep_n92_120"] = {"seed": 0, "K": 100, "targets": sweep}
+        if args.only in (None, "serve"):
+            Ns = list(range(32, 161))
+            Es = list(ex.map(lambda N: run_one(N, 0, serve_steps(N)), Ns))
+            data["serve_n32_160"] = {
+                "seed": 0, "K": 100, "instance": 0,
+                "targets": {str(N): {"E": E, "steps": serve_steps(N)} for N, E in zip(Ns, Es)},
+            }
+            print(f"serve: {len(Ns)} targets ({time.time() - t0:.0f}s)", flush=True)
+    with open(OUT, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    print("wrote", OUT)
+
+
+if __name__ == "__main__":
+    main()
