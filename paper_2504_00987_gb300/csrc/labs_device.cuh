@@ -102,10 +102,16 @@ __device__ __forceinline__ void shr_uniform(const uint32_t (&in)[NW], int s, uin
 // Flip bit i (warp-uniform) of an NW-word vector.
 template <int NW>
 __device__ __forceinline__ void flip_bit(uint32_t (&v)[NW], int i) {
-    const int wi = i >> 5;
-    const uint32_t m = 1u << (i & 31);
+    if constexpr (NW == 2) {  // one 64-bit one-hot mask
+        const uint64_t m = 1ull << i;
+        v[0] ^= static_cast<uint32_t>(m);
+        v[1] ^= static_cast<uint32_t>(m >> 32);
+    } else {
+        const int wi = i >> 5;
+        const uint32_t m = 1u << (i & 31);
 #pragma unroll
-    for (int w = 0; w < NW; ++w) v[w] ^= (w == wi) ? m : 0u;
+        for (int w = 0; w < NW; ++w) v[w] ^= (w == wi) ? m : 0u;
+    }
 }
 
 // Full-width reversal: bit (32*NW - 1 - i) of out = bit i of in.
