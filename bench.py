@@ -36,7 +36,7 @@ SM_COUNT_GB300 = 152
 INT32_LANES_PER_SM = 128  # 4 SM sub-partitions x 32 lanes
 SM_MAX_MHZ_GB300 = 2070.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "mts_kernel_n64_traffic.json")
-KERNEL_SOURCES = ["tabu_core.cuh", "mts.cu", "labs_device.cuh", "kernels.h"]
+KERNEL_SOURCES = ["tabu_core.cuh", "replica.cuh", "mts.cu", "labs_device.cuh", "kernels.h"]
 
 
 def kernel_hash() -> str:
