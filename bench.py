@@ -561,6 +561,41 @@ def run_serve(args) -> None:
         }), flush=True)
 
 
+def run_skew(args) -> None:
+    """d(S) of Appendix A for 100,000 random N=120 sequences (even N: rotations x deletions)."""
+    torch, dev, pg, world, rank = gpu_context(args)
+    import numpy as np
+
+    import paper_2504_00987_gb300 as labs
+    from paper_2504_00987_gb300 import workloads
+
+    n, B = 120, args.replicas or 100_000
+    seqs = torch.from_numpy(workloads.random_sequences(n, B, seed=5).view(np.int64)).to(dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        labs.skew_deviation_batch(seqs, n)
+    ms = statistics.mean(timed_launch(torch, lambda: labs.skew_deviation_batch(seqs, n), stream)[0]
+                         for _ in range(args.steps))
+    ms = parallel.max_over_ranks(pg, [ms], dev)[0]
+    line = {"metric": "sequences/s", "value": B * world / (ms / 1e3), "unit": "sequences/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"skew_deviation_n120: {B} random sequences, d(S) over 120 rotations x 120 deletions"}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        host = seqs[:200].cpu().numpy().view(np.uint64)
+        t0 = time.perf_counter()
+        for b in range(len(host)):
+            oracle.skew_deviation(host[b], n)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": len(host) / dt, "unit": "sequences/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {len(host)} sequences, one core"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -571,7 +606,7 @@ def main() -> None:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--replicas", type=int, default=0, help="profiling only: override replicas")
     ap.add_argument("--steps-per-replica", type=int, default=0, help="profiling only: override budget")
-    ap.add_argument("--workload", choices=["replicas_n64", "sweep_n92_120", "tts", "batch", "serve"],
+    ap.add_argument("--workload", choices=["replicas_n64", "sweep_n92_120", "tts", "batch", "serve", "skew"],
                     default="replicas_n64")
     ap.add_argument("--runs", type=int, default=50, help="tts: runs per N")
     ap.add_argument("--tts-n", default="", help="tts: comma-separated N (default: all)")
@@ -591,6 +626,8 @@ def main() -> None:
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "skew":
+        run_skew(args)
     else:
         run_gpu(args)
 

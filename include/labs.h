@@ -227,6 +227,20 @@ int32_t labs_mts_run(const labs_params* P, uint64_t seed, uint64_t first_instanc
                      int64_t replicas, labs_result* h_out, labs_stream_t stream);
 
 /*
+ * labs_skew_deviation_batch -- deviation from skew-symmetry d(S) (Appendix A,
+ * Eqs. 5-9) of B sequences.  n_non-skew (Eq. 5) counts, for an odd length
+ * L = 2n - 1, the i in 1..n-1 with s_{n+i} != (-1)^i s_{n-i}.  d(S) is its
+ * minimum over the rotations Rot(S; r) for odd N, and over the rotations
+ * followed by one deletion Del(Rot(S; r); i) for even N (the reading that
+ * reproduces the d column of Table II).  N >= 3 (even N >= 4).
+ *   d_seqs  device, B * W uint64 packed sequences.
+ *   d_d     device, B int32 results.
+ * Asynchronous on `stream`.
+ */
+int32_t labs_skew_deviation_batch(const uint64_t* d_seqs, int32_t N, int64_t B, int32_t* d_d,
+                                  labs_stream_t stream);
+
+/*
  * Batched uneven instances: one persistent launch, captured once in a CUDA
  * graph, in which every warp takes the next instance from a device queue
  * and runs it to its stop condition.  Every instance must be bounded by a

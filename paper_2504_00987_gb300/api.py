@@ -52,6 +52,14 @@ def energy_batch(seqs: torch.Tensor, N: int, with_C: bool = False, stream=None):
     return (E, C) if with_C else E
 
 
+def skew_deviation_batch(seqs: torch.Tensor, N: int, stream=None) -> torch.Tensor:
+    """d(S) of Appendix A (Eqs. 5-9) of each packed sequence."""
+    seqs = _check_seqs(seqs, N)
+    out = torch.empty(seqs.shape[0], dtype=torch.int32, device=seqs.device)
+    nat.check(nat.load().labs_skew_deviation_batch(_ptr(seqs), N, seqs.shape[0], _ptr(out), _stream(stream)))
+    return out
+
+
 def tabu_run(start: torch.Tensor, N: int, seed: int, *, max_iter: int = -1, generation: int = 0,
              first_instance: int = 0, trace_cap: int = 0, stream=None) -> dict:
     """B independent tabu searches (Algorithm 2), one from each start sequence."""

@@ -76,6 +76,7 @@ struct ServeArgs {
 };
 
 size_t mts_smem_per_warp(int N, int K);
+cudaError_t launch_skew(const uint64_t* d_seqs, int N, int64_t B, int32_t* d_out, cudaStream_t stream);
 cudaError_t launch_serve_quantum(const ServeArgs& a, int nwmax, int warps_per_block, cudaStream_t stream);
 cudaError_t batch_prepare(int nwmax, int warps_per_block, size_t smem_per_warp, int* max_blocks_per_sm);
 cudaError_t launch_batch(const BatchArgs& a, int nwmax, int blocks, int warps_per_block,
