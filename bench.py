@@ -380,16 +380,40 @@ def run_sweep(args) -> None:
             "per_N": rows}), flush=True)
 
 
+def fit_exponential(Ns, medians):
+    """OLS of log(median) on N (Table III): a * b^N with 95 % intervals of a and b."""
+    import numpy as np
+
+    x = np.asarray(Ns, dtype=float)
+    y = np.log(np.asarray(medians, dtype=float))
+    A = np.vstack([np.ones_like(x), x]).T
+    coef, *_ = np.linalg.lstsq(A, y, rcond=None)
+    resid = y - A @ coef
+    dof = max(len(x) - 2, 1)
+    s2 = float(resid @ resid) / dof
+    cov = s2 * np.linalg.inv(A.T @ A)
+    from scipy import stats
+
+    tq = float(stats.t.ppf(0.975, dof))
+    la, lb = coef
+    sa, sb = np.sqrt(np.diag(cov))
+    return {"a": float(np.exp(la)), "a_ci": [float(np.exp(la - tq * sa)), float(np.exp(la + tq * sa))],
+            "b": float(np.exp(lb)), "b_ci": [float(np.exp(lb - tq * sb)), float(np.exp(lb + tq * sb))],
+            "N_min_fit": int(min(Ns)), "N_max_fit": int(max(Ns))}
+
+
 def run_tts(args) -> None:
-    """Time to target E (the oracle's one-minute best, tests/golden/targets.json) with every
-    replica of the launch stopped by the global termination flag; p50/p99 over runs with
-    distinct seeds."""
+    """Time to a target E with every replica of the launch stopped by the global
+    termination flag; p50/p99 over runs with distinct seeds, and an a * b^N fit of the
+    median (Table III).  Targets (tests/golden/targets.json): the oracle's one-minute
+    best for N = 92..120, or the exact optimum (exhaustive search) for N = 16..32."""
     torch, dev, pg, world, rank = gpu_context(args)
     import numpy as np
 
     import paper_2504_00987_gb300 as labs
 
-    targets = load_targets("sweep_n92_120")
+    kind = "optimum_n16_32" if args.tts_targets == "optimum" else "sweep_n92_120"
+    targets = load_targets(kind)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     reps = args.replicas or sms * 8
     cap = args.steps_per_replica or 10_000_000
@@ -415,13 +439,17 @@ def run_tts(args) -> None:
                      "p50_s": float(np.percentile(t, 50)), "p99_s": float(np.percentile(t, 99)),
                      "q1_s": float(np.percentile(t, 25)), "q3_s": float(np.percentile(t, 75))})
         print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    fit = None
+    ok_rows = [r for r in rows if np.isfinite(r["p50_s"])]
+    if len(ok_rows) >= 3:
+        fit = fit_exponential([r["N"] for r in ok_rows], [r["p50_s"] for r in ok_rows])
     if rank == 0:
         print(json.dumps({
             "metric": "time-to-target-E p50", "value": statistics.median(r["p50_s"] for r in rows),
             "unit": "s", "n_gpus": world, "higher_is_better": False, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"tts_n92_120: {reps} replicas with the global termination flag, K=100, "
-                                   f"cap {cap} steps, target = oracle one-minute best", "runs_per_N": runs},
-            "per_N": rows}), flush=True)
+            "config": {"workload": f"tts_{kind}: {reps} replicas with the global termination flag, K=100, "
+                                   f"cap {cap} steps per replica", "runs_per_N": runs, "targets": kind},
+            "per_N": rows, "fit_median_a_b_pow_N": fit}), flush=True)
 
 
 def run_batch(args) -> None:
@@ -610,6 +638,8 @@ def main() -> None:
                     default="replicas_n64")
     ap.add_argument("--runs", type=int, default=50, help="tts: runs per N")
     ap.add_argument("--tts-n", default="", help="tts: comma-separated N (default: all)")
+    ap.add_argument("--tts-targets", choices=["oracle", "optimum"], default="oracle",
+                    help="tts: oracle one-minute best (N=92..120) or exact optimum (N=16..32)")
     ap.add_argument("--requests", type=int, default=20_000, help="serve: requests")
     ap.add_argument("--baseline-requests", type=int, default=400, help="serve: plain-form prefix")
     ap.add_argument("--slots", type=int, default=0, help="serve: resident slots")

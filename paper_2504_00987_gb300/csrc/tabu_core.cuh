@@ -363,9 +363,26 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
             }
         }
         // ---- apply: windows of the move, C_k, PC(n), flip, tenure, bestSeqTS
-        uint32_t Xp[NW], Yp[NW];
-        shr_uniform<NW>(B, p, Xp);            // bit k = b_{p+k}
-        shr_uniform<NW>(RL, NB - 1 - p, Yp);  // bit k = b_{p-k}
+        uint32_t Xp[NW], Yp[NW];  // bit k = b_{p+k} and b_{p-k}
+        if constexpr (NW >= 4) {
+            // the windows of j = p, fetched from the lane that owns p (cheaper
+            // than shifting the pivot when the shift network is deep)
+            const int qp = p >> 5, lp = p & 31;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                uint32_t xs = 0, ys = 0;
+#pragma unroll
+                for (int q = 0; q < NW; ++q) {
+                    if (w + q < NW) xs = (q == qp) ? X[q][w] : xs;
+                    if (w <= q) ys = (q == qp) ? Y[q][w] : ys;
+                }
+                Xp[w] = __shfl_sync(kFull, xs, lp);
+                Yp[w] = __shfl_sync(kFull, ys, lp);
+            }
+        } else {
+            shr_uniform<NW>(B, p, Xp);
+            shr_uniform<NW>(RL, NB - 1 - p, Yp);
+        }
         const int32_t sp2 = (Xp[0] & 1u) ? 2 : -2;
         flip_bit<NW>(B, p);
         flip_bit<NW>(RL, NB - 1 - p);

@@ -11,6 +11,8 @@ Two sets, each a fixed amount of oracle work so the file is reproducible
   serve_n32_160 -- for N = 32..160: the best E of one oracle replica (seed 0,
                    instance 0) with 4.3e5 * (64/N)^2 steps, about ten seconds
                    of one core ("the oracle's 10 s best").
+  optimum_n16_32 -- for N = 16..32: the exact minimum of E over all 2^N
+                   sequences (the oracle's exhaustive search).
 
 Usage:  python tests/golden/make_targets.py [--only sweep|serve] [--threads T]
 """
@@ -46,7 +48,7 @@ def run_one(N: int, instance: int, steps: int) -> int:
 
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--only", choices=["sweep", "serve"], default=None)
+    ap.add_argument("--only", choices=["sweep", "serve", "optimum"], default=None)
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
     args = ap.parse_args()
     oracle.build()
@@ -68,6 +70,12 @@ def main() -> None:
                 "targets": {str(N): {"E": E, "steps": serve_steps(N)} for N, E in zip(Ns, Es)},
             }
             print(f"serve: {len(Ns)} targets ({time.time() - t0:.0f}s)", flush=True)
+        if args.only in (None, "optimum"):
+            Ns = list(range(16, 33))
+            opts = list(ex.map(oracle.bruteforce, Ns))
+            data["optimum_n16_32"] = {
+                "targets": {str(N): {"E": E, "minimisers": n} for N, (E, n, _) in zip(Ns, opts)}}
+            print(f"optimum: {len(Ns)} exhaustive minima ({time.time() - t0:.0f}s)", flush=True)
     with open(OUT, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)
     print("wrote", OUT)
