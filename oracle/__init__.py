@@ -30,6 +30,8 @@ MAX_N = 256
 MAX_W = 4
 REPLACE_RANDOM = 0
 REPLACE_WORST = 1
+VARIANT_UNIFORM_CROSSOVER = 1
+VARIANT_FIX_FIRST_SPIN = 2
 STATUS_BUDGET = 0
 STATUS_REACHED = 1
 P_COMB_U32 = 3865470566  # floor(0.9 * 2^32), Sec. III.A: p_comb = 0.9
@@ -64,6 +66,7 @@ class Params(ctypes.Structure):
         ("max_generations", ctypes.c_int64),
         ("max_steps", ctypes.c_int64),
         ("max_iter", ctypes.c_int32),
+        ("variant", ctypes.c_int32),
     ]
 
 
@@ -120,6 +123,12 @@ def lib():
                 ctypes.c_int64, i64p,
             ]
             L.orc_tabu_run.restype = ctypes.c_int64
+            L.orc_tabu_run_v.argtypes = [
+                u64p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, u64p, i32p, i32p,
+                ctypes.c_int64, i64p,
+            ]
+            L.orc_tabu_run_v.restype = ctypes.c_int64
             L.orc_mts_run.argtypes = [
                 P(Params), ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, P(Result), i32p,
                 ctypes.c_int64, i64p, P(GenLog), ctypes.c_int64, i64p,
@@ -222,16 +231,16 @@ def neighbour_energies(words, N: int) -> np.ndarray:
 
 
 def tabu_run(start, N: int, seed: int, instance: int, g: int = 0, max_iter: int = -1,
-             step_budget: int = -1, incremental: bool = True, trace_cap: int = 0):
+             step_budget: int = -1, incremental: bool = True, trace_cap: int = 0, variant: int = 0):
     """One tabu search (Algorithm 2).  Returns (best_words, best_E, steps, trace[n,4])."""
     w = _words(start, N)
     best = np.zeros(MAX_W, dtype=np.uint64)
     bestE = np.zeros(1, dtype=np.int32)
     tr = np.zeros((max(trace_cap, 1), 4), dtype=np.int32)
     tl = np.zeros(1, dtype=np.int64)
-    steps = lib().orc_tabu_run(
+    steps = lib().orc_tabu_run_v(
         _ptr(w, ctypes.c_uint64), N, seed, instance, g, max_iter, step_budget, int(incremental),
-        _ptr(best, ctypes.c_uint64), _ptr(bestE, ctypes.c_int32),
+        variant, _ptr(best, ctypes.c_uint64), _ptr(bestE, ctypes.c_int32),
         _ptr(tr, ctypes.c_int32) if trace_cap > 0 else None, trace_cap, _ptr(tl, ctypes.c_int64),
     )
     if steps < 0:
@@ -241,9 +250,10 @@ def tabu_run(start, N: int, seed: int, instance: int, g: int = 0, max_iter: int 
 
 def make_params(N: int, K: int = 100, *, p_comb_u32: int = P_COMB_U32, p_mut: int | None = None,
                 replace_policy: int = REPLACE_RANDOM, target_E: int = -1,
-                max_generations: int = -1, max_steps: int = -1, max_iter: int = -1) -> Params:
+                max_generations: int = -1, max_steps: int = -1, max_iter: int = -1,
+                variant: int = 0) -> Params:
     return Params(N, K, p_comb_u32, p_mut_u32(N) if p_mut is None else p_mut, replace_policy,
-                  target_E, max_generations, max_steps, max_iter)
+                  target_E, max_generations, max_steps, max_iter, variant)
 
 
 def mts_run(params: Params, seed: int, instance: int = 0, incremental: bool = True,

@@ -222,10 +222,11 @@ static int32_t tabu_len(int32_t N, uint64_t seed, uint32_t instance, uint32_t g,
 }
 
 /* s: in = start sequence, out = bestSeqTS.  *E: in = E(start), out = E(best). */
+/* fix_first: s_1 is never flipped (Sec. II.B symmetry break variant). */
 static tabu_info tabu_search(int8_t* s, int32_t N, int32_t* E, uint64_t seed, uint32_t instance,
                              uint32_t g, int32_t max_iter_opt, int64_t step_budget,
-                             int32_t incremental, int32_t* trace, int64_t trace_cap,
-                             int64_t* trace_len) {
+                             int32_t incremental, int32_t fix_first, int32_t* trace,
+                             int64_t trace_cap, int64_t* trace_len) {
     tabu_info info;
     int8_t pivot[ORC_MAX_N], best[ORC_MAX_N];
     int32_t tabu_list[ORC_MAX_N];
@@ -258,11 +259,12 @@ static tabu_info tabu_search(int8_t* s, int32_t N, int32_t* E, uint64_t seed, ui
         }
         /* Admissible minimum and its ties, ascending index order. */
         int32_t m = INT32_MAX, count = 0;
-        for (int j = 0; j < N; ++j) {
+        const int j0 = fix_first ? 1 : 0;
+        for (int j = j0; j < N; ++j) {
             int adm = tabu_list[j] < t || Ej[j] < E_best;
             if (adm && Ej[j] < m) m = Ej[j];
         }
-        for (int j = 0; j < N; ++j) {
+        for (int j = j0; j < N; ++j) {
             int adm = tabu_list[j] < t || Ej[j] < E_best;
             if (adm && Ej[j] == m) ++count;
         }
@@ -271,7 +273,7 @@ static tabu_info tabu_search(int8_t* s, int32_t N, int32_t* E, uint64_t seed, ui
         uint32_t u_ten = draw(seed, instance, g, (uint32_t)t, ORC_PURPOSE_STEP, 1);
         int32_t pick = (int32_t)(((uint64_t)u_tie * (uint64_t)count) >> 32);
         int i_sel = -1;
-        for (int j = 0, seen = 0; j < N; ++j) {
+        for (int j = j0, seen = 0; j < N; ++j) {
             int adm = tabu_list[j] < t || Ej[j] < E_best;
             if (adm && Ej[j] == m) {
                 if (seen == pick) {
@@ -309,13 +311,22 @@ int64_t orc_tabu_run(const uint64_t* start, int32_t N, uint64_t seed, uint32_t i
                      uint32_t g, int32_t max_iter, int64_t step_budget, int32_t incremental,
                      uint64_t* best_out, int32_t* bestE_out, int32_t* trace, int64_t trace_cap,
                      int64_t* trace_len) {
+    return orc_tabu_run_v(start, N, seed, instance, g, max_iter, step_budget, incremental, 0,
+                          best_out, bestE_out, trace, trace_cap, trace_len);
+}
+
+int64_t orc_tabu_run_v(const uint64_t* start, int32_t N, uint64_t seed, uint32_t instance,
+                       uint32_t g, int32_t max_iter, int64_t step_budget, int32_t incremental,
+                       int32_t variant, uint64_t* best_out, int32_t* bestE_out, int32_t* trace,
+                       int64_t trace_cap, int64_t* trace_len) {
     if (N < 3 || N > ORC_MAX_N || !start) return -1;
     int8_t s[ORC_MAX_N];
     unpack(start, N, s);
     int32_t E = (int32_t)energy_spins(s, N, 0);
     if (trace_len) *trace_len = 0;
     tabu_info info = tabu_search(s, N, &E, seed, instance, g, max_iter, step_budget, incremental,
-                                 trace, trace_cap, trace_len);
+                                 (variant & ORC_VARIANT_FIX_FIRST_SPIN) != 0, trace, trace_cap,
+                                 trace_len);
     if (best_out) pack(s, N, best_out);
     if (bestE_out) *bestE_out = E;
     return info.steps;
@@ -339,6 +350,10 @@ int64_t orc_tabu_run(const uint64_t* start, int32_t N, uint64_t seed, uint32_t i
 /*    highest-E member, lowest index on ties (replace-worst variant);        */
 /*  - a step budget may end a tabu search early; that generation still      */
 /*    completes with the partial bestSeqTS.                                  */
+/* Variants: uniform crossover takes bit j from P2 iff word j%4 of           */
+/* (instance, g, j/4, CROSS) < 2^31; fixing s_1 = +1 complements the initial */
+/* members with s_1 = -1 (E is unchanged, Sec. II.B), never mutates s_1 and  */
+/* never flips it in the tabu search.                                        */
 /* Draw layout per generation g:                                             */
 /*   GEN(g,0): x coin, y tournament a, z tournament b, w tournament c        */
 /*   GEN(g,1): x tournament d, y cut, z sample, w maxIter                    */
@@ -357,6 +372,7 @@ static int params_ok(const orc_params* P) {
     if (P->K < 1 || P->K > ORC_MAX_K) return 0;
     if (P->replace_policy != ORC_REPLACE_RANDOM && P->replace_policy != ORC_REPLACE_WORST) return 0;
     if (P->target_E < 0 && P->max_generations < 0 && P->max_steps < 0) return 0;
+    if (P->variant & ~(ORC_VARIANT_UNIFORM_CROSSOVER | ORC_VARIANT_FIX_FIRST_SPIN)) return 0;
     return 1;
 }
 
@@ -384,6 +400,8 @@ int32_t orc_mts_run(const orc_params* P, uint64_t seed, uint32_t instance, int32
             words[w] = (uint64_t)lo | ((uint64_t)hi << 32);
         }
         unpack(words, N, pop + (size_t)p * N);
+        if ((P->variant & ORC_VARIANT_FIX_FIRST_SPIN) && pop[(size_t)p * N] < 0)
+            for (int i = 0; i < N; ++i) pop[(size_t)p * N + i] = (int8_t)-pop[(size_t)p * N + i];
         popE[p] = (int32_t)energy_spins(pop + (size_t)p * N, N, 0);
     }
     /* bestSeq <- the lowest-energy member (lowest index on ties). */
@@ -419,8 +437,16 @@ int32_t orc_mts_run(const orc_params* P, uint64_t seed, uint32_t instance, int32
             int p1 = tournament(popE, a, b);
             int p2 = tournament(popE, c, d);
             int cut = rand_int(1, N - 1, draw(seed, instance, gg, 1, ORC_PURPOSE_GEN, 1));
-            for (int i = 0; i < N; ++i)
-                child[i] = i < cut ? pop[(size_t)p1 * N + i] : pop[(size_t)p2 * N + i];
+            if (P->variant & ORC_VARIANT_UNIFORM_CROSSOVER) {
+                cut = 0;
+                for (int i = 0; i < N; ++i) {
+                    uint32_t u = draw(seed, instance, gg, (uint32_t)(i / 4), ORC_PURPOSE_CROSS, i % 4);
+                    child[i] = u < 0x80000000u ? pop[(size_t)p2 * N + i] : pop[(size_t)p1 * N + i];
+                }
+            } else {
+                for (int i = 0; i < N; ++i)
+                    child[i] = i < cut ? pop[(size_t)p1 * N + i] : pop[(size_t)p2 * N + i];
+            }
             L.crossover = 1;
             L.p1 = p1;
             L.p2 = p2;
@@ -433,7 +459,7 @@ int32_t orc_mts_run(const orc_params* P, uint64_t seed, uint32_t instance, int32
         pack(child, N, L.pre_mut);
 
         /* Mutate(child, p_mutate): independent flip per bit. */
-        for (int j = 0; j < N; ++j) {
+        for (int j = (P->variant & ORC_VARIANT_FIX_FIRST_SPIN) ? 1 : 0; j < N; ++j) {
             uint32_t u = draw(seed, instance, gg, (uint32_t)(j / 4), ORC_PURPOSE_MUT, j % 4);
             if (u < P->p_mut_u32) child[j] = (int8_t)-child[j];
         }
@@ -443,7 +469,8 @@ int32_t orc_mts_run(const orc_params* P, uint64_t seed, uint32_t instance, int32
         int32_t E_child = (int32_t)energy_spins(child, N, 0);
         int64_t budget = P->max_steps >= 0 ? P->max_steps - steps : -1;
         tabu_info ti = tabu_search(child, N, &E_child, seed, instance, gg, P->max_iter, budget,
-                                   incremental, trace, trace_cap, trace_len);
+                                   incremental, (P->variant & ORC_VARIANT_FIX_FIRST_SPIN) != 0,
+                                   trace, trace_cap, trace_len);
         steps += ti.steps;
         pack(child, N, L.post_tabu);
 

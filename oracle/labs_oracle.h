@@ -43,6 +43,11 @@ extern "C" {
 #define ORC_PURPOSE_GEN 2u  /* (instance, generation g, 0|1|2) -> per-generation */
 #define ORC_PURPOSE_MUT 3u  /* (instance, g, j/4)   -> word (j%4) per bit j      */
 #define ORC_PURPOSE_STEP 4u /* (instance, g, t)     -> x: tie pick, y: tenure    */
+#define ORC_PURPOSE_CROSS 5u /* (instance, g, j/4)  -> word (j%4): uniform crossover */
+
+/* Variants (bit flags of orc_params.variant). */
+#define ORC_VARIANT_UNIFORM_CROSSOVER 1 /* Combine: bit j from P2 iff its draw < 2^31 */
+#define ORC_VARIANT_FIX_FIRST_SPIN 2    /* s_1 = +1 throughout (Sec. II.B) */
 
 #define ORC_REPLACE_RANDOM 0 /* Algorithm 1: replace a random individual */
 #define ORC_REPLACE_WORST 1  /* variant: replace the highest-E member     */
@@ -60,6 +65,7 @@ typedef struct orc_params {
     int64_t max_generations;  /* -1: none */
     int64_t max_steps;        /* tabu steps per replica; -1: none */
     int32_t max_iter;         /* tabu length; -1: floor(N/2) + randInt(0, N) */
+    int32_t variant;          /* ORC_VARIANT_* flags, 0: Algorithm 1 as read */
 } orc_params;
 
 typedef struct orc_result {
@@ -109,6 +115,11 @@ int64_t orc_tabu_run(const uint64_t* start, int32_t N, uint64_t seed, uint32_t i
                      uint32_t g, int32_t max_iter, int64_t step_budget, int32_t incremental,
                      uint64_t* best_out, int32_t* bestE_out, int32_t* trace, int64_t trace_cap,
                      int64_t* trace_len);
+/* The same with variant flags (ORC_VARIANT_FIX_FIRST_SPIN keeps s_1 fixed). */
+int64_t orc_tabu_run_v(const uint64_t* start, int32_t N, uint64_t seed, uint32_t instance,
+                       uint32_t g, int32_t max_iter, int64_t step_budget, int32_t incremental,
+                       int32_t variant, uint64_t* best_out, int32_t* bestE_out, int32_t* trace,
+                       int64_t trace_cap, int64_t* trace_len);
 
 /* Algorithm 1 for one replica.  trace (nullable): {g, t, j, E} per tabu
  * step and {g, 0, replace, E_child} at the end of each generation.

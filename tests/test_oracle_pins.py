@@ -201,7 +201,7 @@ def test_table2_skew_deviation(orc):
 # ---------------------------------------------------------------- Tabu search
 
 
-def replay_tabu(orc, start_s, N, trace, seed, instance, g, max_iter):
+def replay_tabu(orc, start_s, N, trace, seed, instance, g, max_iter, fix_first=False):
     """Brute-force replay of one tabu search: every neighbour energy from
     numpy.correlate, the admissible set and its minima enumerated directly,
     the random picks taken from the (pinned) Philox draws."""
@@ -218,7 +218,7 @@ def replay_tabu(orc, start_s, N, trace, seed, instance, g, max_iter):
             u = s.copy()
             u[i] = -u[i]
             Ej.append(np_energy(u)[0])
-        adm = [i for i in range(N) if tabu[i] < t or Ej[i] < E_best]
+        adm = [i for i in range(1 if fix_first else 0, N) if tabu[i] < t or Ej[i] < E_best]
         m = min(Ej[i] for i in adm)
         ties = [i for i in adm if Ej[i] == m]
         x, y, _, _ = orc.philox4x32_10([instance, g, t, 4], key)
@@ -286,13 +286,18 @@ def replay_mts(orc, P, seed, inst, res, genlog):
     def ri(lo, hi, u):
         return lo + ((u * (hi - lo + 1)) >> 32)
 
+    uniform = bool(P.variant & orc.VARIANT_UNIFORM_CROSSOVER)
+    fix = bool(P.variant & orc.VARIANT_FIX_FIRST_SPIN)
     pop = []
     for p in range(K):
         bits = []
         for w in range(W):
             word = draw(p, w, 1, 0) | (draw(p, w, 1, 1) << 32)
             bits += [1 if (word >> b) & 1 else -1 for b in range(64)]
-        pop.append(np.array(bits[:N]))
+        member = np.array(bits[:N])
+        if fix and member[0] < 0:  # Sec. II.B: complement so that s_1 = +1
+            member = -member
+        pop.append(member)
     popE = [np_energy(s)[0] for s in pop]
     bestE = min(popE)
     for L in genlog:
@@ -303,20 +308,27 @@ def replay_mts(orc, P, seed, inst, res, genlog):
             c, d = ri(0, K - 1, draw(g, 0, 2, 3)), ri(0, K - 1, draw(g, 1, 2, 0))
             win = lambda x, y: x if (popE[x], x) <= (popE[y], y) else y
             assert L.crossover == 1 and L.p1 == win(a, b) and L.p2 == win(c, d)
-            cut = ri(1, N - 1, draw(g, 1, 2, 1))
-            assert L.cut == cut
-            expect = np.concatenate([pop[L.p1][:cut], pop[L.p2][cut:]])
+            if uniform:
+                take2 = np.array([draw(g, i // 4, 5, i % 4) < (1 << 31) for i in range(N)])
+                expect = np.where(take2, pop[L.p2], pop[L.p1])
+            else:
+                cut = ri(1, N - 1, draw(g, 1, 2, 1))
+                assert L.cut == cut
+                expect = np.concatenate([pop[L.p1][:cut], pop[L.p2][cut:]])
         else:
             assert L.crossover == 0 and L.p1 == ri(0, K - 1, draw(g, 1, 2, 2))
             expect = pop[L.p1]
         assert np.array_equal(pre_mut, expect)
-        flips = np.array([-1 if draw(g, j // 4, 3, j % 4) < P.p_mut_u32 else 1 for j in range(N)])
+        flips = np.array([-1 if draw(g, j // 4, 3, j % 4) < P.p_mut_u32 and not (fix and j == 0) else 1
+                          for j in range(N)])
         pre_tabu = orc.words_to_spins(list(L.pre_tabu)[:W], N)
         assert np.array_equal(pre_tabu, pre_mut * flips)
         mi = P.max_iter if P.max_iter >= 0 else N // 2 + ri(0, N, draw(g, 1, 2, 3))
         assert L.max_iter == mi and L.min_tabu == mi // 10 and L.max_tabu == (12 * mi) // 100
         child = orc.words_to_spins(list(L.post_tabu)[:W], N)
         assert np_energy(child)[0] == L.E_child <= np_energy(pre_tabu)[0]
+        if fix:
+            assert child[0] == 1 and pre_tabu[0] == 1
         bestE = min(bestE, L.E_child)
         if P.replace_policy == 0:
             slot = ri(0, K - 1, draw(g, 2, 2, 0))
@@ -336,6 +348,31 @@ def test_mts_replay(orc, N, K, policy):
     res, tr, gl = orc.mts_run(P, seed=42, instance=3, trace_cap=100000, genlog_cap=100)
     replay_mts(orc, P, 42, 3, res, gl)
     assert res["status"] == orc.STATUS_BUDGET
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("N,K", [(9, 6), (40, 30), (70, 12)])
+def test_mts_variants_replay(orc, N, K, variant):
+    """Uniform crossover (bit j from P2 iff its CROSS draw < 2^31) and s_1 = +1
+    fixed (Sec. II.B): replayed generation by generation; with s_1 fixed no tabu
+    step ever flips bit 0."""
+    P = orc.make_params(N, K, max_generations=25, variant=variant)
+    res, tr, gl = orc.mts_run(P, seed=5, instance=2, trace_cap=100000, genlog_cap=100)
+    replay_mts(orc, P, 5, 2, res, gl)
+    if variant & orc.VARIANT_FIX_FIRST_SPIN:
+        assert all(int(r[2]) != 0 for r in tr if r[1] > 0)
+        assert orc.words_to_spins(res["seq"], N)[0] == 1
+
+
+@pytest.mark.parametrize("N", [6, 11, 16])
+def test_tabu_fixed_first_spin_replay(orc, N):
+    rng = np.random.default_rng(40 + N)
+    s = rand_spins(rng, N)
+    best, bestE, steps, tr = orc.tabu_run(orc.spins_to_words(s), N, 7, 1, 2, trace_cap=1000, variant=2)
+    x = orc.philox4x32_10([1, 2, 1, 2], [7, 0])[3]
+    max_iter = N // 2 + ((int(x) * (N + 1)) >> 32)
+    E_rep, best_rep = replay_tabu(orc, s, N, tr, 7, 1, 2, max_iter, fix_first=True)
+    assert E_rep == bestE and np.array_equal(orc.words_to_spins(best, N), best_rep)
 
 
 @pytest.mark.parametrize("N", [5, 12, 33, 66])
