@@ -402,32 +402,20 @@ def fit_exponential(Ns, medians):
             "N_min_fit": int(min(Ns)), "N_max_fit": int(max(Ns))}
 
 
-def run_tts(args) -> None:
-    """Time to a target E with every replica of the launch stopped by the global
-    termination flag; p50/p99 over runs with distinct seeds, and an a * b^N fit of the
-    median (Table III).  Targets (tests/golden/targets.json): the oracle's one-minute
-    best for N = 92..120, or the exact optimum (exhaustive search) for N = 16..32."""
-    torch, dev, pg, world, rank = gpu_context(args)
+def tts_rows(torch, labs, Ns, targets, reps, cap, runs, stream, variant=0, replace_policy=0):
+    """Per N: `runs` launches of `reps` replicas (seeds 1000, 1001, ...) that stop,
+    all of them, as soon as one reaches targets[N]; seconds to target per run."""
     import numpy as np
 
-    import paper_2504_00987_gb300 as labs
-
-    kind = "optimum_n16_32" if args.tts_targets == "optimum" else "sweep_n92_120"
-    targets = load_targets(kind)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    reps = args.replicas or sms * 8
-    cap = args.steps_per_replica or 10_000_000
-    runs = args.runs
-    stream = torch.cuda.current_stream()
-    Ns = [int(x) for x in args.tts_n.split(",")] if args.tts_n else sorted(targets)
     rows = []
     for n in Ns:
         target = targets[n]
-        P = labs.make_params(n, 100, target_E=target, max_steps=cap, glf=True)
-        labs.mts_launch(labs.make_params(n, 100, max_steps=1000), 0, 0, reps)
+        P = labs.make_params(n, 100, target_E=target, max_steps=cap, glf=True, variant=variant,
+                             replace_policy=replace_policy)
+        labs.mts_launch(labs.make_params(n, 100, max_steps=1000, variant=variant), 0, 0, reps)
         times, reached = [], 0
         for run in range(runs):
-            flag = torch.zeros(1, dtype=torch.int32, device=dev)
+            flag = torch.zeros(1, dtype=torch.int32, device=stream.device)
             ms, out = timed_launch(torch, lambda: labs.mts_launch(P, 1000 + run, 0, reps, glf_flag=flag,
                                                                   stream=stream), stream)
             res = labs.decode_results(out, n)
@@ -437,19 +425,107 @@ def run_tts(args) -> None:
         t = np.array(times)
         rows.append({"N": n, "target_E": target, "runs": runs, "reached": reached,
                      "p50_s": float(np.percentile(t, 50)), "p99_s": float(np.percentile(t, 99)),
-                     "q1_s": float(np.percentile(t, 25)), "q3_s": float(np.percentile(t, 75))})
-        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
-    fit = None
+                     "q1_s": float(np.percentile(t, 25)), "q3_s": float(np.percentile(t, 75)),
+                     "times_s": [round(x, 6) for x in times]})
+        print(json.dumps({k: v for k, v in rows[-1].items() if k != "times_s"}), file=sys.stderr, flush=True)
+    return rows
+
+
+def median_fit(rows):
+    import numpy as np
+
     ok_rows = [r for r in rows if np.isfinite(r["p50_s"])]
-    if len(ok_rows) >= 3:
-        fit = fit_exponential([r["N"] for r in ok_rows], [r["p50_s"] for r in ok_rows])
+    if len(ok_rows) < 3:
+        return None
+    return fit_exponential([r["N"] for r in ok_rows], [r["p50_s"] for r in ok_rows])
+
+
+def run_tts(args) -> None:
+    """Time to a target E with every replica of the launch stopped by the global
+    termination flag; p50/p99 over runs with distinct seeds, and an a * b^N fit of the
+    median (Table III).  Targets (tests/golden/targets.json): the oracle's one-minute
+    best for N = 92..120, or the exact optimum (exhaustive search) for N = 16..32."""
+    torch, dev, pg, world, rank = gpu_context(args)
+    import paper_2504_00987_gb300 as labs
+
+    kind = "optimum_n16_32" if args.tts_targets == "optimum" else "sweep_n92_120"
+    targets = load_targets(kind)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    reps = args.replicas or sms * 8
+    cap = args.steps_per_replica or 10_000_000
+    stream = torch.cuda.current_stream()
+    Ns = [int(x) for x in args.tts_n.split(",")] if args.tts_n else sorted(targets)
+    rows = tts_rows(torch, labs, Ns, targets, reps, cap, args.runs, stream)
+    for r in rows:
+        r.pop("times_s")
     if rank == 0:
         print(json.dumps({
             "metric": "time-to-target-E p50", "value": statistics.median(r["p50_s"] for r in rows),
             "unit": "s", "n_gpus": world, "higher_is_better": False, "dtype": "int32", "data": "synthetic",
             "config": {"workload": f"tts_{kind}: {reps} replicas with the global termination flag, K=100, "
-                                   f"cap {cap} steps per replica", "runs_per_N": runs, "targets": kind},
-            "per_N": rows, "fit_median_a_b_pow_N": fit}), flush=True)
+                                   f"cap {cap} steps per replica", "runs_per_N": args.runs, "targets": kind},
+            "per_N": rows, "fit_median_a_b_pow_N": median_fit(rows)}), flush=True)
+
+
+# Policies compared by the A/B time-to-target workload: the default reading of
+# Algorithm 1 and one change each (replace-worst, uniform crossover, s_1 = +1).
+AB_POLICIES = [
+    ("one_point+replace_random", 0, 0),
+    ("one_point+replace_worst", 0, 1),
+    ("uniform+replace_random", 1, 0),
+    ("one_point+replace_random+s1_fixed", 2, 0),
+    ("uniform+replace_worst+s1_fixed", 3, 1),
+]
+
+
+def run_tts_ab(args) -> None:
+    """A/B time to target of the population policies, same N, targets, seeds and
+    replica count for each; per N the Mann-Whitney U test of each policy's run
+    times against the default's (two-sided; runs that miss count as +inf)."""
+    torch, dev, pg, world, rank = gpu_context(args)
+    import numpy as np
+    from scipy import stats
+
+    import paper_2504_00987_gb300 as labs
+
+    kind = "optimum_n16_32" if args.tts_targets == "optimum" else "sweep_n92_120"
+    targets = load_targets(kind)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    reps = args.replicas or sms * 8
+    cap = args.steps_per_replica or 10_000_000
+    stream = torch.cuda.current_stream()
+    Ns = [int(x) for x in args.tts_n.split(",")] if args.tts_n else sorted(targets)[:5]
+    out = {}
+    for name, variant, policy in AB_POLICIES:
+        print(f"# {name}", file=sys.stderr, flush=True)
+        out[name] = tts_rows(torch, labs, Ns, targets, reps, cap, args.runs, stream, variant=variant,
+                             replace_policy=policy)
+    base = out[AB_POLICIES[0][0]]
+    summary = []
+    for name, variant, policy in AB_POLICIES:
+        rows = out[name]
+        per_n = []
+        for r, b in zip(rows, base):
+            big = 1e9  # a run that missed ranks after every run that reached
+            x = np.minimum(np.array(r["times_s"]), big)
+            y = np.minimum(np.array(b["times_s"]), big)
+            p = float(stats.mannwhitneyu(x, y, alternative="two-sided").pvalue) if name != AB_POLICIES[0][0] else None
+            per_n.append({"N": r["N"], "reached": r["reached"], "p50_s": r["p50_s"], "q1_s": r["q1_s"],
+                          "q3_s": r["q3_s"], "p50_ratio_vs_default": r["p50_s"] / b["p50_s"],
+                          "mannwhitney_p_vs_default": p})
+        summary.append({"policy": name, "variant": variant, "replace_policy": policy,
+                        "per_N": per_n, "fit_median_a_b_pow_N": median_fit(rows),
+                        "geomean_p50_ratio_vs_default": float(np.exp(np.mean(np.log(
+                            [q["p50_ratio_vs_default"] for q in per_n]))))})
+    if rank == 0:
+        print(json.dumps({
+            "metric": "time-to-target-E p50 ratio vs default policy (geomean over N)",
+            "value": min(s["geomean_p50_ratio_vs_default"] for s in summary[1:]),
+            "unit": "ratio", "n_gpus": world, "higher_is_better": False, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"tts_ab_{kind}: {len(AB_POLICIES)} policies, N={Ns}, {reps} replicas with "
+                                   f"the global termination flag, K=100, cap {cap} steps per replica",
+                       "runs_per_N": args.runs, "targets": kind},
+            "policies": summary}), flush=True)
 
 
 def run_batch(args) -> None:
@@ -634,10 +710,11 @@ def main() -> None:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--replicas", type=int, default=0, help="profiling only: override replicas")
     ap.add_argument("--steps-per-replica", type=int, default=0, help="profiling only: override budget")
-    ap.add_argument("--workload", choices=["replicas_n64", "sweep_n92_120", "tts", "batch", "serve", "skew"],
+    ap.add_argument("--workload", choices=["replicas_n64", "sweep_n92_120", "tts", "tts_ab", "batch", "serve",
+                                           "skew"],
                     default="replicas_n64")
     ap.add_argument("--runs", type=int, default=50, help="tts: runs per N")
-    ap.add_argument("--tts-n", default="", help="tts: comma-separated N (default: all)")
+    ap.add_argument("--tts-n", default="", help="tts: comma-separated N (default: all; tts_ab: first five)")
     ap.add_argument("--tts-targets", choices=["oracle", "optimum"], default="oracle",
                     help="tts: oracle one-minute best (N=92..120) or exact optimum (N=16..32)")
     ap.add_argument("--requests", type=int, default=20_000, help="serve: requests")
@@ -652,6 +729,8 @@ def main() -> None:
         run_sweep(args)
     elif args.workload == "tts":
         run_tts(args)
+    elif args.workload == "tts_ab":
+        run_tts_ab(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "serve":

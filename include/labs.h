@@ -54,6 +54,13 @@ extern "C" {
 #define LABS_REPLACE_RANDOM 0 /* Algorithm 1: a uniformly drawn member (default) */
 #define LABS_REPLACE_WORST 1  /* variant: the highest-E member, lowest index on ties */
 
+/* Variants of the population loop (bit flags; 0 = Algorithm 1 as read). */
+#define LABS_VARIANT_UNIFORM_CROSSOVER 1 /* Combine: child bit j from P2 iff draw (i, g, j/4, 5)
+                                            word j%4 < 2^31 (instead of one cut) */
+#define LABS_VARIANT_FIX_FIRST_SPIN 2    /* s_1 = +1 throughout (Sec. II.B symmetry break):
+                                            initial members with s_1 = -1 are complemented,
+                                            s_1 is never mutated nor flipped by the tabu search */
+
 /* Why a replica stopped. */
 #define LABS_RUN_BUDGET 0  /* generation or step budget used up */
 #define LABS_RUN_REACHED 1 /* E(best) <= target_E */
@@ -102,6 +109,8 @@ typedef struct labs_params {
                                 (t >= 1: tabu step; t == 0: end of generation g with
                                 j = replaced member, E = E(child)) */
     int64_t trace_cap;       /* records per replica in d_trace */
+    int32_t variant;         /* LABS_VARIANT_* flags */
+    int32_t pad;
 } labs_params;
 
 /* Per-replica result in device memory (64 bytes). */
@@ -136,6 +145,8 @@ typedef struct labs_tabu_opts {
     uint32_t generation;     /* g of the draws (a search inside MTS uses its generation) */
     uint64_t first_instance; /* sequence b uses instance first_instance + b */
     int64_t trace_cap;       /* records {g, t, j, E} per sequence in d_trace */
+    int32_t variant;         /* LABS_VARIANT_FIX_FIRST_SPIN: bit 0 is never flipped */
+    int32_t pad;
 } labs_tabu_opts;
 
 /*
@@ -150,7 +161,7 @@ typedef struct labs_instance {
     uint32_t p_comb_u32, p_mut_u32;
     int32_t replace_policy, target_E;
     int64_t max_generations, max_steps;
-    int32_t max_iter, pad;
+    int32_t max_iter, variant;
     uint64_t seed;
     uint64_t instance;
 } labs_instance;

@@ -42,6 +42,8 @@ EXPORTED = [
     "labs_serve_destroy", "labs_skew_deviation_batch",
 ]
 STATIC_MAX_REPLICAS = 4096
+VARIANT_UNIFORM_CROSSOVER = 1
+VARIANT_FIX_FIRST_SPIN = 2
 ORDER_LPT = 0
 ORDER_GIVEN = 1
 
@@ -66,6 +68,8 @@ class Params(ctypes.Structure):
         ("glf", ctypes.c_int32),
         ("d_trace", ctypes.c_void_p),
         ("trace_cap", ctypes.c_int64),
+        ("variant", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
     ]
 
 
@@ -103,6 +107,8 @@ class TabuOpts(ctypes.Structure):
         ("generation", ctypes.c_uint32),
         ("first_instance", ctypes.c_uint64),
         ("trace_cap", ctypes.c_int64),
+        ("variant", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
     ]
 
 
@@ -117,7 +123,7 @@ class Instance(ctypes.Structure):
         ("max_generations", ctypes.c_int64),
         ("max_steps", ctypes.c_int64),
         ("max_iter", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("variant", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
         ("instance", ctypes.c_uint64),
     ]

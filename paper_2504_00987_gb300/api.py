@@ -61,7 +61,7 @@ def skew_deviation_batch(seqs: torch.Tensor, N: int, stream=None) -> torch.Tenso
 
 
 def tabu_run(start: torch.Tensor, N: int, seed: int, *, max_iter: int = -1, generation: int = 0,
-             first_instance: int = 0, trace_cap: int = 0, stream=None) -> dict:
+             first_instance: int = 0, trace_cap: int = 0, variant: int = 0, stream=None) -> dict:
     """B independent tabu searches (Algorithm 2), one from each start sequence."""
     start = _check_seqs(start, N)
     B, dev = start.shape[0], start.device
@@ -69,7 +69,7 @@ def tabu_run(start: torch.Tensor, N: int, seed: int, *, max_iter: int = -1, gene
     bestE = torch.empty(B, dtype=torch.int32, device=dev)
     steps = torch.empty(B, dtype=torch.int64, device=dev)
     trace = torch.zeros((B, trace_cap, 4), dtype=torch.int32, device=dev) if trace_cap > 0 else None
-    opts = nat.TabuOpts(max_iter, generation, first_instance, trace_cap)
+    opts = nat.TabuOpts(max_iter, generation, first_instance, trace_cap, variant, 0)
     nat.check(nat.load().labs_tabu_run(_ptr(start), N, B, seed, ctypes.byref(opts), _ptr(best),
                                        _ptr(bestE), _ptr(steps), _ptr(trace), _stream(stream)))
     return {"best": best, "bestE": bestE, "steps": steps, "trace": trace}
@@ -78,12 +78,12 @@ def tabu_run(start: torch.Tensor, N: int, seed: int, *, max_iter: int = -1, gene
 def make_params(N: int, K: int = 100, *, p_comb_u32: int = P_COMB_U32, p_mut: int = 0,
                 replace_policy: int = nat.REPLACE_RANDOM, target_E: int = -1,
                 max_generations: int = -1, max_steps: int = -1, max_iter: int = -1,
-                glf: bool = False, trace: torch.Tensor | None = None) -> nat.Params:
+                glf: bool = False, trace: torch.Tensor | None = None, variant: int = 0) -> nat.Params:
     """labs_params; `trace` is an int32 CUDA tensor of shape (replicas, cap, 4) or None."""
     cap = 0 if trace is None else int(trace.shape[1])
     ptr = None if trace is None else trace.data_ptr()
     return nat.Params(N, K, p_comb_u32, p_mut, replace_policy, target_E, max_generations,
-                      max_steps, max_iter, 1 if glf else 0, ptr, cap)
+                      max_steps, max_iter, 1 if glf else 0, ptr, cap, variant, 0)
 
 
 def mts_launch(params: nat.Params, seed: int, first_instance: int, replicas: int,
@@ -145,9 +145,9 @@ def mts_run(params: nat.Params, seed: int, first_instance: int, replicas: int, s
 def make_instance(N: int, K: int = 100, *, seed: int = 0, instance: int = 0, max_steps: int = -1,
                   max_generations: int = -1, target_E: int = -1, p_comb_u32: int = P_COMB_U32,
                   p_mut: int = 0, replace_policy: int = nat.REPLACE_RANDOM,
-                  max_iter: int = -1) -> nat.Instance:
+                  max_iter: int = -1, variant: int = 0) -> nat.Instance:
     return nat.Instance(N, K, p_comb_u32, p_mut, replace_policy, target_E, max_generations,
-                        max_steps, max_iter, 0, seed, instance)
+                        max_steps, max_iter, variant, seed, instance)
 
 
 def _inst_array(instances):

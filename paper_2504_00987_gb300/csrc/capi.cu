@@ -88,6 +88,12 @@ int32_t check_run(int32_t N, int32_t K, int32_t replace_policy, int32_t target_E
     return LABS_OK;
 }
 
+int32_t check_variant(int32_t variant, const char* who) {
+    if (variant & ~(LABS_VARIANT_UNIFORM_CROSSOVER | LABS_VARIANT_FIX_FIRST_SPIN))
+        return fail(LABS_EINVAL, "%s: unknown variant flags 0x%x", who, variant);
+    return LABS_OK;
+}
+
 uint32_t default_p_mut(int32_t N, uint32_t p_mut_u32) {
     return p_mut_u32 != 0 ? p_mut_u32 : static_cast<uint32_t>((1ull << 32) / N);
 }
@@ -131,6 +137,7 @@ int32_t make_mts_args(const labs_params* P, uint64_t seed, uint64_t first_instan
         return fail(LABS_EINVAL, "too many replicas for one launch");
     if (P->trace_cap < 0) return fail(LABS_EINVAL, "trace_cap < 0");
     if (P->d_trace != nullptr) LABS_TRY(check_dev(P->d_trace, 16, "d_trace", false));
+    LABS_TRY(check_variant(P->variant, "params"));
     const size_t per_warp = lgpu::mts_smem_per_warp(P->N, P->K);
     if (per_warp * lgpu::kWarpsPerBlock > 227u * 1024u)
         return fail(LABS_EINVAL, "population does not fit in shared memory (N=%d, K=%d)", P->N, P->K);
@@ -144,6 +151,7 @@ int32_t make_mts_args(const labs_params* P, uint64_t seed, uint64_t first_instan
     a->max_generations = P->max_generations;
     a->max_steps = P->max_steps;
     a->max_iter = P->max_iter;
+    a->variant = P->variant;
     a->seed = seed;
     a->first_instance = first_instance;
     a->replicas = replicas;
@@ -187,6 +195,7 @@ int32_t labs_tabu_run(const uint64_t* d_start, int32_t N, int64_t B, uint64_t se
     if (opts->max_iter < -1 || opts->max_iter > (1 << 20))
         return fail(LABS_EINVAL, "max_iter=%d outside -1..2^20", opts->max_iter);
     if (opts->trace_cap < 0) return fail(LABS_EINVAL, "trace_cap < 0");
+    LABS_TRY(check_variant(opts->variant, "opts"));
     if (opts->first_instance + static_cast<uint64_t>(B) > 0x100000000ull)
         return fail(LABS_EINVAL, "instances beyond 2^32 - 1");
     if (B == 0) return ok();
@@ -204,6 +213,7 @@ int32_t labs_tabu_run(const uint64_t* d_start, int32_t N, int64_t B, uint64_t se
     a.first_instance = opts->first_instance;
     a.generation = opts->generation;
     a.max_iter = opts->max_iter;
+    a.variant = opts->variant;
     a.d_best = d_best;
     a.d_bestE = d_bestE;
     a.d_steps = d_steps;

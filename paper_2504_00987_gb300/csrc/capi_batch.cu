@@ -53,6 +53,7 @@ int32_t validate_instances(const labs_instance* h, int64_t n) {
         snprintf(who, sizeof who, "instance %lld", static_cast<long long>(i));
         LABS_TRY(check_run(x.N, x.K, x.replace_policy, x.target_E, x.max_generations, x.max_steps,
                            x.max_iter, x.instance, 1, who));
+        LABS_TRY(check_variant(x.variant, who));
     }
     return LABS_OK;
 }

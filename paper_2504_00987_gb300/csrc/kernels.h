@@ -17,7 +17,7 @@ struct MtsArgs {
     uint32_t p_comb_u32, p_mut_u32;
     int32_t replace_policy, target_E;
     int64_t max_generations, max_steps;
-    int32_t max_iter;
+    int32_t max_iter, variant;
     uint64_t seed, first_instance;
     int64_t replicas;
     labs_device_result* d_out;
@@ -33,7 +33,7 @@ struct TabuArgs {
     int64_t B;
     uint64_t seed, first_instance;
     uint32_t generation;
-    int32_t max_iter;
+    int32_t max_iter, variant;
     uint64_t* d_best;
     int32_t* d_bestE;
     int64_t* d_steps;

@@ -20,6 +20,7 @@ constexpr uint32_t kPurposeInit = 1u;
 constexpr uint32_t kPurposeGen = 2u;
 constexpr uint32_t kPurposeMut = 3u;
 constexpr uint32_t kPurposeStep = 4u;
+constexpr uint32_t kPurposeCross = 5u;
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
 // 32x32->64 multiplications by fixed odd constants with a Weyl-sequence key

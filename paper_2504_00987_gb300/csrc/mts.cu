@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) mts_kernel(const MtsArgs 
     cfg.max_generations = a.max_generations;
     cfg.max_steps = a.max_steps;
     cfg.max_iter = a.max_iter;
+    cfg.variant = a.variant;
     cfg.inst = static_cast<uint32_t>(a.first_instance + static_cast<uint64_t>(r));
     cfg.key = philox_key(a.seed);
     int4* trace = a.d_trace ? a.d_trace + r * a.trace_cap : nullptr;
@@ -59,8 +60,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) tabu_kernel(const TabuArg
     }
     int4* trace = a.d_trace ? a.d_trace + b * a.trace_cap : nullptr;
     int64_t trace_len = 0;
-    const TabuOut to = tabu_search<NW, TRACE>(seq, N, key, inst, a.generation, max_iter, -1,
-                                       Cs_all[warp], trace, a.trace_cap, trace_len, lane);
+    const TabuOut to =
+        (a.variant & LABS_VARIANT_FIX_FIRST_SPIN)
+            ? tabu_search<NW, TRACE, true>(seq, N, key, inst, a.generation, max_iter, -1, Cs_all[warp],
+                                           trace, a.trace_cap, trace_len, lane)
+            : tabu_search<NW, TRACE, false>(seq, N, key, inst, a.generation, max_iter, -1, Cs_all[warp],
+                                            trace, a.trace_cap, trace_len, lane);
     if (lane < NW) {
         uint32_t v = 0;
 #pragma unroll

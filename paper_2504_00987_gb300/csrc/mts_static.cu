@@ -77,6 +77,7 @@ extern "C" int32_t labs_mts_run_static(const labs_params* P, uint64_t seed, uint
         return fail(LABS_EINVAL, "replicas=%lld exceeds the static scratch maximum of %lld",
                     static_cast<long long>(replicas), static_cast<long long>(kMaxReplicas));
     if (P->trace_cap < 0) return fail(LABS_EINVAL, "trace_cap < 0");
+    LABS_TRY(check_variant(P->variant, "params"));
     if (P->d_trace != nullptr) LABS_TRY(check_dev(P->d_trace, 16, "d_trace", false));
     const size_t per_warp = lgpu::mts_smem_per_warp(P->N, P->K);
     if (per_warp * lgpu::kWarpsPerBlock > 227u * 1024u)
@@ -99,6 +100,7 @@ extern "C" int32_t labs_mts_run_static(const labs_params* P, uint64_t seed, uint
     a.max_generations = P->max_generations;
     a.max_steps = P->max_steps;
     a.max_iter = P->max_iter;
+    a.variant = P->variant;
     a.seed = seed;
     a.first_instance = first_instance;
     a.replicas = replicas;

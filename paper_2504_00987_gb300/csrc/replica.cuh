@@ -19,9 +19,35 @@ struct ReplicaCfg {
     int32_t replace_policy, target_E;
     int64_t max_generations, max_steps;
     int32_t max_iter;
+    int32_t variant;  // LABS_VARIANT_* flags
     uint32_t inst;
     uint2 key;
 };
+
+// Bit j of `mask` is set iff word j%4 of Philox(inst, g, j/4, purpose) < thr
+// (j < N): one Philox block per four bits, nibbles OR-reduced over the warp.
+template <int NW>
+__device__ __forceinline__ void draw_bit_mask(const ReplicaCfg& a, uint32_t g, uint32_t purpose,
+                                              uint32_t thr, int lane, uint32_t (&mask)[NW]) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) mask[w] = 0u;
+    const int nd = (a.N + 3) / 4;
+    for (int base = 0; base < nd; base += 32) {
+        const int cidx = base + lane;
+        uint32_t nib = 0;
+        if (cidx < nd) {
+            const uint4 d = draw4(a.key, a.inst, g, static_cast<uint32_t>(cidx), purpose);
+            nib = (d.x < thr ? 1u : 0u) | (d.y < thr ? 2u : 0u) | (d.z < thr ? 4u : 0u) |
+                  (d.w < thr ? 8u : 0u);
+        }
+        const int word_of = cidx >> 3;  // 8 nibbles per 32-bit word
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t part = (word_of == w) ? (nib << (4 * (cidx & 7))) : 0u;
+            mask[w] |= __reduce_or_sync(kFull, part) & word_lowmask(w, a.N);
+        }
+    }
+}
 
 template <int NW>
 struct ReplicaState {
@@ -69,6 +95,13 @@ __device__ void replica_init(const ReplicaCfg& a, uint32_t* __restrict__ pop,
         pop[p * NW + 2 * w64 + 1] = d.y & word_lowmask(2 * w64 + 1, N);
     }
     __syncwarp();
+    if (a.variant & LABS_VARIANT_FIX_FIRST_SPIN) {  // complement members with s_1 = -1 (E unchanged)
+        for (int p = lane; p < K; p += 32)
+            if ((pop[p * NW] & 1u) == 0u)
+#pragma unroll
+                for (int w = 0; w < NW; ++w) pop[p * NW + w] ^= word_lowmask(w, N);
+        __syncwarp();
+    }
     int32_t lbestE = INT_MAX;
     int lbest = INT_MAX;
     for (int p = lane; p < K; p += 32) {
@@ -133,37 +166,39 @@ __device__ int64_t replica_generation(const ReplicaCfg& a, ReplicaState<NW>& st,
     if (coin < a.p_comb_u32) {
         const int p1 = tournament(popE, rand_int(0, K - 1, ua), rand_int(0, K - 1, ub));
         const int p2 = tournament(popE, rand_int(0, K - 1, uc), rand_int(0, K - 1, ud));
-        const int cut = rand_int(1, N - 1, ucut);
+        if (a.variant & LABS_VARIANT_UNIFORM_CROSSOVER) {
+            uint32_t m2[NW];  // bits taken from P2
+            draw_bit_mask<NW>(a, gg, kPurposeCross, 0x80000000u, lane, m2);
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const uint32_t lm = word_lowmask(w, cut);
-            child[w] = (pop[p1 * NW + w] & lm) | (pop[p2 * NW + w] & ~lm);
+            for (int w = 0; w < NW; ++w) child[w] = (pop[p1 * NW + w] & ~m2[w]) | (pop[p2 * NW + w] & m2[w]);
+        } else {
+            const int cut = rand_int(1, N - 1, ucut);
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                const uint32_t lm = word_lowmask(w, cut);
+                child[w] = (pop[p1 * NW + w] & lm) | (pop[p2 * NW + w] & ~lm);
+            }
         }
     } else {
         load_seq<NW>(pop + rand_int(0, K - 1, usamp) * NW, child);
     }
     // Mutate: bit j flips iff word j%4 of (inst, g, j/4, MUT) < p_mut.
-    const int nmut = (N + 3) / 4;
-    for (int base = 0; base < nmut; base += 32) {
-        const int cidx = base + lane;
-        uint32_t nib = 0;
-        if (cidx < nmut) {
-            const uint4 d = draw4(a.key, a.inst, gg, static_cast<uint32_t>(cidx), kPurposeMut);
-            nib = (d.x < p_mut ? 1u : 0u) | (d.y < p_mut ? 2u : 0u) | (d.z < p_mut ? 4u : 0u) |
-                  (d.w < p_mut ? 8u : 0u);
-        }
-        const int word_of = cidx >> 3;  // 8 nibbles per 32-bit word
+    {
+        uint32_t mm[NW];
+        draw_bit_mask<NW>(a, gg, kPurposeMut, p_mut, lane, mm);
+        if (a.variant & LABS_VARIANT_FIX_FIRST_SPIN) mm[0] &= ~1u;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const uint32_t part = (word_of == w) ? (nib << (4 * (cidx & 7))) : 0u;
-            child[w] ^= __reduce_or_sync(kFull, part) & word_lowmask(w, N);
-        }
+        for (int w = 0; w < NW; ++w) child[w] ^= mm[w];
     }
     // child <- Tabu-Search(child)
     const int max_iter = a.max_iter >= 0 ? a.max_iter : N / 2 + rand_int(0, N, uiter);
     const int64_t budget = a.max_steps >= 0 ? a.max_steps - st.steps : -1;
-    const TabuOut to = tabu_search<NW, TRACE>(child, N, a.key, a.inst, gg, max_iter, budget, Cs, trace,
-                                       trace_cap, trace_len, lane);
+    const TabuOut to =
+        (a.variant & LABS_VARIANT_FIX_FIRST_SPIN)
+            ? tabu_search<NW, TRACE, true>(child, N, a.key, a.inst, gg, max_iter, budget, Cs, trace,
+                                           trace_cap, trace_len, lane)
+            : tabu_search<NW, TRACE, false>(child, N, a.key, a.inst, gg, max_iter, budget, Cs, trace,
+                                            trace_cap, trace_len, lane);
     st.steps += to.steps;
     if (to.E_best < st.E_best) {
         st.E_best = to.E_best;

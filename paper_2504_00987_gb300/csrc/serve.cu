@@ -26,6 +26,7 @@ __device__ __forceinline__ ReplicaCfg serve_cfg(const labs_instance& in) {
     c.max_generations = in.max_generations;
     c.max_steps = in.max_steps;
     c.max_iter = in.max_iter;
+    c.variant = in.variant;
     c.inst = static_cast<uint32_t>(in.instance);
     c.key = philox_key(in.seed);
     return c;

@@ -220,9 +220,10 @@ __device__ __forceinline__ int plane_count(const int32_t (&c)[NW]) {
 
 // One tabu search from `seq` (warp-uniform).  On return `seq` holds
 // bestSeqTS.  Draws: step t uses Philox(instance, g, t, 4): x tie, y tenure.
+// FIX_FIRST: bit 0 (s_1) is never a candidate move.
 // `Cs` is warp-private shared scratch of 32*NW ints.  With TRACE, `trace`
 // receives {g, t, j, E} per step while trace_len < trace_cap.
-template <int NW, bool TRACE>
+template <int NW, bool TRACE, bool FIX_FIRST = false>
 __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key,
                                const uint32_t inst, const uint32_t g, const int max_iter,
                                const int64_t budget, int32_t* __restrict__ Cs,
@@ -269,7 +270,7 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
         const int j = lane + 32 * q;
         Lq[q] = min(j, N - 1 - j);
         mir[q] = j < N ? N - 1 - j : 0;
-        jvalid |= (j < N ? 1u : 0u) << q;
+        jvalid |= (j < N && !(FIX_FIRST && j == 0) ? 1u : 0u) << q;
 #pragma unroll
         for (int w = 0; w <= q && w + q < NW; ++w)
             mmask[q][w] = word_lowmask(w, Lq[q] + 1) & (w == 0 ? ~1u : kFull);

@@ -56,7 +56,7 @@ def test_argument_errors_without_gpu(lib):
     assert lib.labs_energy_batch(None, 257, 1, None, None, None) == nat.LABS_EINVAL
     assert lib.labs_energy_batch(None, 64, -1, None, None, None) == nat.LABS_EINVAL
     assert lib.labs_energy_batch(None, 64, 0, None, None, None) == nat.LABS_OK  # empty batch
-    P = nat.Params(64, 100, 0, 0, 0, -1, -1, -1, -1, 0, None, 0)  # no budget at all
+    P = nat.Params(64, 100, 0, 0, 0, -1, -1, -1, -1, 0, None, 0, 0, 0)  # no budget at all
     res = (nat.Result * 1)()
     assert lib.labs_mts_run(ctypes.byref(P), 0, 0, 1, res, None) == nat.LABS_EINVAL
     assert b"unbounded" in lib.labs_last_error()
@@ -69,7 +69,12 @@ def test_argument_errors_without_gpu(lib):
     P.replace_policy = 0
     assert lib.labs_mts_run(ctypes.byref(P), 0, 2**32 - 1, 2, res, None) == nat.LABS_EINVAL
     assert lib.labs_mts_run(ctypes.byref(P), 0, 0, 0, res, None) == nat.LABS_OK  # no replicas
-    opts = nat.TabuOpts(-2, 0, 0, 0)
+    P.variant = 4  # no such flag
+    assert lib.labs_mts_run(ctypes.byref(P), 0, 0, 1, res, None) == nat.LABS_EINVAL
+    assert b"variant" in lib.labs_last_error()
+    assert lib.labs_mts_run_static(ctypes.byref(P), 0, 0, 1, res, None) == nat.LABS_EINVAL
+    P.variant = 0
+    opts = nat.TabuOpts(-2, 0, 0, 0, 0, 0)
     assert lib.labs_tabu_run(None, 64, 1, 0, ctypes.byref(opts), None, None, None, None, None) == nat.LABS_EINVAL
 
 
@@ -77,8 +82,8 @@ def test_struct_sizes():
     from paper_2504_00987_gb300 import _native as nat
 
     assert ctypes.sizeof(nat.DeviceResult) == 64
-    assert ctypes.sizeof(nat.Params) == 4 * 6 + 8 * 2 + 4 * 2 + 8 + 8
-    assert ctypes.sizeof(nat.TabuOpts) == 24
+    assert ctypes.sizeof(nat.Params) == 4 * 6 + 8 * 2 + 4 * 2 + 8 + 8 + 8
+    assert ctypes.sizeof(nat.TabuOpts) == 32
 
 
 def test_no_oracle_in_product():
@@ -101,6 +106,10 @@ def test_batch_argument_errors_without_gpu(lib):
     m = nat.Mapping()
     assert lib.labs_autotune(arr, 2, None, ctypes.byref(m)) == nat.LABS_EINVAL
     assert b"instance 1" in lib.labs_last_error()
+    arr[1].max_steps, arr[1].variant = 10, 16
+    assert lib.labs_autotune(arr, 2, None, ctypes.byref(m)) == nat.LABS_EINVAL
+    assert b"variant" in lib.labs_last_error()
+    arr[1].max_steps, arr[1].variant = -1, 0
     h = ctypes.c_void_p()
     bad_map = nat.Mapping(3, 1, 0, 0)
     arr[1].max_steps = 10
