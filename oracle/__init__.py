@@ -32,6 +32,7 @@ REPLACE_RANDOM = 0
 REPLACE_WORST = 1
 VARIANT_UNIFORM_CROSSOVER = 1
 VARIANT_FIX_FIRST_SPIN = 2
+VARIANT_SKEW = 4  # odd N: skew-symmetric sequences only (Sec. II.C)
 STATUS_BUDGET = 0
 STATUS_REACHED = 1
 P_COMB_U32 = 3865470566  # floor(0.9 * 2^32), Sec. III.A: p_comb = 0.9
@@ -252,8 +253,10 @@ def make_params(N: int, K: int = 100, *, p_comb_u32: int = P_COMB_U32, p_mut: in
                 replace_policy: int = REPLACE_RANDOM, target_E: int = -1,
                 max_generations: int = -1, max_steps: int = -1, max_iter: int = -1,
                 variant: int = 0) -> Params:
-    return Params(N, K, p_comb_u32, p_mut_u32(N) if p_mut is None else p_mut, replace_policy,
-                  target_E, max_generations, max_steps, max_iter, variant)
+    if p_mut is None:  # 1/(number of spins mutation acts on)
+        p_mut = p_mut_u32((N + 1) // 2 if variant & VARIANT_SKEW else N)
+    return Params(N, K, p_comb_u32, p_mut, replace_policy, target_E, max_generations, max_steps,
+                  max_iter, variant)
 
 
 def mts_run(params: Params, seed: int, instance: int = 0, incremental: bool = True,

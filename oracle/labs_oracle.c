@@ -307,6 +307,103 @@ static tabu_info tabu_search(int8_t* s, int32_t N, int32_t* E, uint64_t seed, ui
     return info;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Skew-symmetric restriction (Sec. II.C).  For odd N = 2n - 1 a sequence is */
+/* skew-symmetric iff s_{n+i} = (-1)^i s_{n-i} for i = 1..n-1; 0-based with  */
+/* centre c = n - 1 that is s[c+i] = (-1)^i s[c-i].  The n spins s[0..c]   */
+/* are free and determine the rest.                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Rewrites s[c+1..N-1] from the free half s[0..c-1]. */
+static void symmetrize(int8_t* s, int32_t N) {
+    const int c = (N - 1) / 2;
+    for (int i = 1; i <= c; ++i) s[c + i] = (int8_t)((i & 1) ? -s[c - i] : s[c - i]);
+}
+
+/* Tabu search over skew-symmetric sequences: move i (0 <= i <= c) flips the
+ * free spin s[i] and, for i < c, its partner s[N-1-i], so the pivot stays
+ * skew-symmetric.  Everything else is Algorithm 2 as read above, over the n
+ * moves: maxIter = floor(n/2) + randInt(0, n) unless given, the tenure
+ * bounds from maxIter, tabuList indexed by move, the same admissibility,
+ * ties and draws.  Neighbour energies straight from Eq. 2. */
+static tabu_info tabu_search_skew(int8_t* s, int32_t N, int32_t* E, uint64_t seed,
+                                  uint32_t instance, uint32_t g, int32_t max_iter_opt,
+                                  int64_t step_budget, int32_t fix_first, int32_t* trace,
+                                  int64_t trace_cap, int64_t* trace_len) {
+    tabu_info info;
+    const int c = (N - 1) / 2, n = c + 1;
+    int8_t pivot[ORC_MAX_N], best[ORC_MAX_N];
+    int32_t tabu_list[ORC_MAX_N];
+    int32_t Ei[ORC_MAX_N];
+
+    info.max_iter = tabu_len(n, seed, instance, g, max_iter_opt);
+    info.min_tabu = info.max_iter / 10;
+    info.max_tabu = (12 * info.max_iter) / 100;
+    info.steps = 0;
+
+    memcpy(pivot, s, (size_t)N);
+    memcpy(best, s, (size_t)N);
+    for (int i = 0; i < n; ++i) tabu_list[i] = 0;
+    int32_t E_best = *E;
+
+    for (int32_t t = 1; t <= info.max_iter; ++t) {
+        if (step_budget >= 0 && info.steps >= step_budget) break;
+        /* Energies of the n neighbours: flip s[i] and its partner. */
+        for (int i = 0; i < n; ++i) {
+            pivot[i] = (int8_t)-pivot[i];
+            if (i < c) pivot[N - 1 - i] = (int8_t)-pivot[N - 1 - i];
+            Ei[i] = (int32_t)energy_spins(pivot, N, 0);
+            pivot[i] = (int8_t)-pivot[i];
+            if (i < c) pivot[N - 1 - i] = (int8_t)-pivot[N - 1 - i];
+        }
+        int32_t m = INT32_MAX, count = 0;
+        const int i0 = fix_first ? 1 : 0;
+        for (int i = i0; i < n; ++i) {
+            int adm = tabu_list[i] < t || Ei[i] < E_best;
+            if (adm && Ei[i] < m) m = Ei[i];
+        }
+        for (int i = i0; i < n; ++i) {
+            int adm = tabu_list[i] < t || Ei[i] < E_best;
+            if (adm && Ei[i] == m) ++count;
+        }
+        if (count == 0) break; /* cannot happen while maxTabu < n - 1 */
+        uint32_t u_tie = draw(seed, instance, g, (uint32_t)t, ORC_PURPOSE_STEP, 0);
+        uint32_t u_ten = draw(seed, instance, g, (uint32_t)t, ORC_PURPOSE_STEP, 1);
+        int32_t pick = (int32_t)(((uint64_t)u_tie * (uint64_t)count) >> 32);
+        int i_sel = -1;
+        for (int i = i0, seen = 0; i < n; ++i) {
+            int adm = tabu_list[i] < t || Ei[i] < E_best;
+            if (adm && Ei[i] == m) {
+                if (seen == pick) {
+                    i_sel = i;
+                    break;
+                }
+                ++seen;
+            }
+        }
+        if (i_sel < 0) break; /* unreachable: pick < count */
+        pivot[i_sel] = (int8_t)-pivot[i_sel];
+        if (i_sel < c) pivot[N - 1 - i_sel] = (int8_t)-pivot[N - 1 - i_sel];
+        tabu_list[i_sel] = t + rand_int(info.min_tabu, info.max_tabu, u_ten);
+        if (m < E_best) {
+            E_best = m;
+            memcpy(best, pivot, (size_t)N);
+        }
+        ++info.steps;
+        if (trace && trace_len && *trace_len < trace_cap) {
+            int32_t* r = trace + 4 * (*trace_len);
+            r[0] = (int32_t)g;
+            r[1] = t;
+            r[2] = i_sel;
+            r[3] = m;
+            ++*trace_len;
+        }
+    }
+    memcpy(s, best, (size_t)N);
+    *E = E_best;
+    return info;
+}
+
 int64_t orc_tabu_run(const uint64_t* start, int32_t N, uint64_t seed, uint32_t instance,
                      uint32_t g, int32_t max_iter, int64_t step_budget, int32_t incremental,
                      uint64_t* best_out, int32_t* bestE_out, int32_t* trace, int64_t trace_cap,
@@ -320,13 +417,18 @@ int64_t orc_tabu_run_v(const uint64_t* start, int32_t N, uint64_t seed, uint32_t
                        int32_t variant, uint64_t* best_out, int32_t* bestE_out, int32_t* trace,
                        int64_t trace_cap, int64_t* trace_len) {
     if (N < 3 || N > ORC_MAX_N || !start) return -1;
+    const int skew = (variant & ORC_VARIANT_SKEW) != 0;
+    if (skew && N % 2 == 0) return -1;
     int8_t s[ORC_MAX_N];
     unpack(start, N, s);
+    if (skew) symmetrize(s, N); /* the start's free half decides */
     int32_t E = (int32_t)energy_spins(s, N, 0);
     if (trace_len) *trace_len = 0;
-    tabu_info info = tabu_search(s, N, &E, seed, instance, g, max_iter, step_budget, incremental,
-                                 (variant & ORC_VARIANT_FIX_FIRST_SPIN) != 0, trace, trace_cap,
-                                 trace_len);
+    const int fix = (variant & ORC_VARIANT_FIX_FIRST_SPIN) != 0;
+    tabu_info info = skew ? tabu_search_skew(s, N, &E, seed, instance, g, max_iter, step_budget, fix,
+                                             trace, trace_cap, trace_len)
+                          : tabu_search(s, N, &E, seed, instance, g, max_iter, step_budget,
+                                        incremental, fix, trace, trace_cap, trace_len);
     if (best_out) pack(s, N, best_out);
     if (bestE_out) *bestE_out = E;
     return info.steps;
@@ -353,7 +455,10 @@ int64_t orc_tabu_run_v(const uint64_t* start, int32_t N, uint64_t seed, uint32_t
 /* Variants: uniform crossover takes bit j from P2 iff word j%4 of           */
 /* (instance, g, j/4, CROSS) < 2^31; fixing s_1 = +1 complements the initial */
 /* members with s_1 = -1 (E is unchanged, Sec. II.B), never mutates s_1 and  */
-/* never flips it in the tabu search.                                        */
+/* never flips it in the tabu search.  The skew variant (odd N) keeps every */
+/* sequence skew-symmetric: initial members are symmetrized, the cut is     */
+/* randInt(1, n-1) and mutation and uniform crossover act on the n free     */
+/* spins, the child is symmetrized, and the tabu search is the skew one.    */
 /* Draw layout per generation g:                                             */
 /*   GEN(g,0): x coin, y tournament a, z tournament b, w tournament c        */
 /*   GEN(g,1): x tournament d, y cut, z sample, w maxIter                    */
@@ -372,7 +477,9 @@ static int params_ok(const orc_params* P) {
     if (P->K < 1 || P->K > ORC_MAX_K) return 0;
     if (P->replace_policy != ORC_REPLACE_RANDOM && P->replace_policy != ORC_REPLACE_WORST) return 0;
     if (P->target_E < 0 && P->max_generations < 0 && P->max_steps < 0) return 0;
-    if (P->variant & ~(ORC_VARIANT_UNIFORM_CROSSOVER | ORC_VARIANT_FIX_FIRST_SPIN)) return 0;
+    if (P->variant & ~(ORC_VARIANT_UNIFORM_CROSSOVER | ORC_VARIANT_FIX_FIRST_SPIN | ORC_VARIANT_SKEW))
+        return 0;
+    if ((P->variant & ORC_VARIANT_SKEW) && P->N % 2 == 0) return 0;
     return 1;
 }
 
@@ -381,6 +488,8 @@ int32_t orc_mts_run(const orc_params* P, uint64_t seed, uint32_t instance, int32
                     orc_genlog* genlog, int64_t genlog_cap, int64_t* genlog_len) {
     if (!params_ok(P) || !res) return -1;
     const int32_t N = P->N, K = P->K, W = words_for(N);
+    const int skew = (P->variant & ORC_VARIANT_SKEW) != 0;
+    const int32_t nfree = skew ? (N + 1) / 2 : N; /* spins crossover and mutation act on */
     int8_t* pop = (int8_t*)malloc((size_t)K * (size_t)N);
     int32_t* popE = (int32_t*)malloc(sizeof(int32_t) * (size_t)K);
     if (!pop || !popE) {
@@ -400,6 +509,7 @@ int32_t orc_mts_run(const orc_params* P, uint64_t seed, uint32_t instance, int32
             words[w] = (uint64_t)lo | ((uint64_t)hi << 32);
         }
         unpack(words, N, pop + (size_t)p * N);
+        if (skew) symmetrize(pop + (size_t)p * N, N);
         if ((P->variant & ORC_VARIANT_FIX_FIRST_SPIN) && pop[(size_t)p * N] < 0)
             for (int i = 0; i < N; ++i) pop[(size_t)p * N + i] = (int8_t)-pop[(size_t)p * N + i];
         popE[p] = (int32_t)energy_spins(pop + (size_t)p * N, N, 0);
@@ -436,10 +546,10 @@ int32_t orc_mts_run(const orc_params* P, uint64_t seed, uint32_t instance, int32
             int d = rand_int(0, K - 1, draw(seed, instance, gg, 1, ORC_PURPOSE_GEN, 0));
             int p1 = tournament(popE, a, b);
             int p2 = tournament(popE, c, d);
-            int cut = rand_int(1, N - 1, draw(seed, instance, gg, 1, ORC_PURPOSE_GEN, 1));
+            int cut = rand_int(1, nfree - 1, draw(seed, instance, gg, 1, ORC_PURPOSE_GEN, 1));
             if (P->variant & ORC_VARIANT_UNIFORM_CROSSOVER) {
                 cut = 0;
-                for (int i = 0; i < N; ++i) {
+                for (int i = 0; i < nfree; ++i) {
                     uint32_t u = draw(seed, instance, gg, (uint32_t)(i / 4), ORC_PURPOSE_CROSS, i % 4);
                     child[i] = u < 0x80000000u ? pop[(size_t)p2 * N + i] : pop[(size_t)p1 * N + i];
                 }
@@ -447,6 +557,7 @@ int32_t orc_mts_run(const orc_params* P, uint64_t seed, uint32_t instance, int32
                 for (int i = 0; i < N; ++i)
                     child[i] = i < cut ? pop[(size_t)p1 * N + i] : pop[(size_t)p2 * N + i];
             }
+            if (skew) symmetrize(child, N);
             L.crossover = 1;
             L.p1 = p1;
             L.p2 = p2;
@@ -459,18 +570,21 @@ int32_t orc_mts_run(const orc_params* P, uint64_t seed, uint32_t instance, int32
         pack(child, N, L.pre_mut);
 
         /* Mutate(child, p_mutate): independent flip per bit. */
-        for (int j = (P->variant & ORC_VARIANT_FIX_FIRST_SPIN) ? 1 : 0; j < N; ++j) {
+        for (int j = (P->variant & ORC_VARIANT_FIX_FIRST_SPIN) ? 1 : 0; j < nfree; ++j) {
             uint32_t u = draw(seed, instance, gg, (uint32_t)(j / 4), ORC_PURPOSE_MUT, j % 4);
             if (u < P->p_mut_u32) child[j] = (int8_t)-child[j];
         }
+        if (skew) symmetrize(child, N);
         pack(child, N, L.pre_tabu);
 
         /* child <- Tabu-Search(child). */
         int32_t E_child = (int32_t)energy_spins(child, N, 0);
         int64_t budget = P->max_steps >= 0 ? P->max_steps - steps : -1;
-        tabu_info ti = tabu_search(child, N, &E_child, seed, instance, gg, P->max_iter, budget,
-                                   incremental, (P->variant & ORC_VARIANT_FIX_FIRST_SPIN) != 0,
-                                   trace, trace_cap, trace_len);
+        const int fix = (P->variant & ORC_VARIANT_FIX_FIRST_SPIN) != 0;
+        tabu_info ti = skew ? tabu_search_skew(child, N, &E_child, seed, instance, gg, P->max_iter,
+                                               budget, fix, trace, trace_cap, trace_len)
+                            : tabu_search(child, N, &E_child, seed, instance, gg, P->max_iter,
+                                          budget, incremental, fix, trace, trace_cap, trace_len);
         steps += ti.steps;
         pack(child, N, L.post_tabu);
 

@@ -13,6 +13,7 @@
  *   - Tabu-Search ........................................... Algorithm 2, Sec. III.B
  *   - tableC / vectorC incremental neighbour energies ....... Table I, Sec. III.C
  *   - deviation from skew-symmetry d(S) ..................... Appendix A, Eqs. 5-9
+ *   - search restricted to skew-symmetric sequences ......... Sec. II.C (variant)
  *   - exhaustive optimum (brute force) for small N .......... Sec. II (definition of S*)
  *
  * Randomness: every random decision is one output word of Philox4x32-10
@@ -48,6 +49,7 @@ extern "C" {
 /* Variants (bit flags of orc_params.variant). */
 #define ORC_VARIANT_UNIFORM_CROSSOVER 1 /* Combine: bit j from P2 iff its draw < 2^31 */
 #define ORC_VARIANT_FIX_FIRST_SPIN 2    /* s_1 = +1 throughout (Sec. II.B) */
+#define ORC_VARIANT_SKEW 4              /* odd N: skew-symmetric sequences only (Sec. II.C) */
 
 #define ORC_REPLACE_RANDOM 0 /* Algorithm 1: replace a random individual */
 #define ORC_REPLACE_WORST 1  /* variant: replace the highest-E member     */
@@ -64,7 +66,8 @@ typedef struct orc_params {
     int32_t target_E;         /* stop when E(best) <= target_E; -1: none */
     int64_t max_generations;  /* -1: none */
     int64_t max_steps;        /* tabu steps per replica; -1: none */
-    int32_t max_iter;         /* tabu length; -1: floor(N/2) + randInt(0, N) */
+    int32_t max_iter;         /* tabu length; -1: floor(N/2) + randInt(0, N)
+                                 (skew variant: n = (N+1)/2 in place of N) */
     int32_t variant;          /* ORC_VARIANT_* flags, 0: Algorithm 1 as read */
 } orc_params;
 

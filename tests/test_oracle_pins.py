@@ -201,30 +201,54 @@ def test_table2_skew_deviation(orc):
 # ---------------------------------------------------------------- Tabu search
 
 
-def replay_tabu(orc, start_s, N, trace, seed, instance, g, max_iter, fix_first=False):
+def skew_complete(s):
+    """Sec. II.C, 1-based: for N = 2n - 1, s_{n+i} = (-1)^i s_{n-i}, i = 1..n-1."""
+    s = np.array(s)
+    N = len(s)
+    n = (N + 1) // 2
+    for i in range(1, n):
+        s[(n + i) - 1] = (-1) ** i * s[(n - i) - 1]
+    return s
+
+
+def is_skew(s):
+    N = len(s)
+    n = (N + 1) // 2
+    return N % 2 == 1 and all(s[n + i - 1] == (-1) ** i * s[n - i - 1] for i in range(1, n))
+
+
+def replay_tabu(orc, start_s, N, trace, seed, instance, g, max_iter, fix_first=False, skew=False):
     """Brute-force replay of one tabu search: every neighbour energy from
     numpy.correlate, the admissible set and its minima enumerated directly,
-    the random picks taken from the (pinned) Philox draws."""
+    the random picks taken from the (pinned) Philox draws.  skew: the moves
+    are the free spins 1..n of Sec. II.C, each flipped with its partner."""
     key = [seed & 0xFFFFFFFF, seed >> 32]
-    s = np.array(start_s)
+    s = skew_complete(start_s) if skew else np.array(start_s)
     E_best = np_energy(s)[0]
     best = s.copy()
-    tabu = np.zeros(N, dtype=np.int64)
+    moves = (N + 1) // 2 if skew else N
+    tabu = np.zeros(moves, dtype=np.int64)
     min_t, max_t = max_iter // 10, (12 * max_iter) // 100
+
+    def flipped(u, i):
+        u = u.copy()
+        u[i] = -u[i]
+        if skew and i != N - 1 - i:
+            u[N - 1 - i] = -u[N - 1 - i]
+        return u
+
     for (gg, t, j, E) in trace:
         assert gg == g
-        Ej = []
-        for i in range(N):
-            u = s.copy()
-            u[i] = -u[i]
-            Ej.append(np_energy(u)[0])
-        adm = [i for i in range(1 if fix_first else 0, N) if tabu[i] < t or Ej[i] < E_best]
+        Ej = [np_energy(flipped(s, i))[0] for i in range(moves)]
+        adm = [i for i in range(1 if fix_first else 0, moves) if tabu[i] < t or Ej[i] < E_best]
         m = min(Ej[i] for i in adm)
         ties = [i for i in adm if Ej[i] == m]
         x, y, _, _ = orc.philox4x32_10([instance, g, t, 4], key)
         assert j == ties[(int(x) * len(ties)) >> 32]
         assert E == m
-        s[j] = -s[j]
+        s = flipped(s, j)
+        if skew:
+            assert is_skew(s)
         tabu[j] = t + min_t + ((int(y) * (max_t - min_t + 1)) >> 32)
         if E < E_best:  # Algorithm 2: bestSeqTS moves only on a strictly lower energy
             E_best, best = E, s.copy()
@@ -288,13 +312,16 @@ def replay_mts(orc, P, seed, inst, res, genlog):
 
     uniform = bool(P.variant & orc.VARIANT_UNIFORM_CROSSOVER)
     fix = bool(P.variant & orc.VARIANT_FIX_FIRST_SPIN)
+    skew = bool(P.variant & orc.VARIANT_SKEW)
+    nf = (N + 1) // 2 if skew else N  # spins that crossover and mutation act on
+    sym = skew_complete if skew else (lambda v: np.array(v))
     pop = []
     for p in range(K):
         bits = []
         for w in range(W):
             word = draw(p, w, 1, 0) | (draw(p, w, 1, 1) << 32)
             bits += [1 if (word >> b) & 1 else -1 for b in range(64)]
-        member = np.array(bits[:N])
+        member = sym(bits[:N])
         if fix and member[0] < 0:  # Sec. II.B: complement so that s_1 = +1
             member = -member
         pop.append(member)
@@ -309,26 +336,28 @@ def replay_mts(orc, P, seed, inst, res, genlog):
             win = lambda x, y: x if (popE[x], x) <= (popE[y], y) else y
             assert L.crossover == 1 and L.p1 == win(a, b) and L.p2 == win(c, d)
             if uniform:
-                take2 = np.array([draw(g, i // 4, 5, i % 4) < (1 << 31) for i in range(N)])
-                expect = np.where(take2, pop[L.p2], pop[L.p1])
+                take2 = np.array([i < nf and draw(g, i // 4, 5, i % 4) < (1 << 31) for i in range(N)])
+                expect = sym(np.where(take2, pop[L.p2], pop[L.p1]))
             else:
-                cut = ri(1, N - 1, draw(g, 1, 2, 1))
+                cut = ri(1, nf - 1, draw(g, 1, 2, 1))
                 assert L.cut == cut
-                expect = np.concatenate([pop[L.p1][:cut], pop[L.p2][cut:]])
+                expect = sym(np.concatenate([pop[L.p1][:cut], pop[L.p2][cut:]]))
         else:
             assert L.crossover == 0 and L.p1 == ri(0, K - 1, draw(g, 1, 2, 2))
             expect = pop[L.p1]
         assert np.array_equal(pre_mut, expect)
-        flips = np.array([-1 if draw(g, j // 4, 3, j % 4) < P.p_mut_u32 and not (fix and j == 0) else 1
-                          for j in range(N)])
+        flips = np.array([-1 if j < nf and draw(g, j // 4, 3, j % 4) < P.p_mut_u32 and not (fix and j == 0)
+                          else 1 for j in range(N)])
         pre_tabu = orc.words_to_spins(list(L.pre_tabu)[:W], N)
-        assert np.array_equal(pre_tabu, pre_mut * flips)
-        mi = P.max_iter if P.max_iter >= 0 else N // 2 + ri(0, N, draw(g, 1, 2, 3))
+        assert np.array_equal(pre_tabu, sym(pre_mut * flips))
+        mi = P.max_iter if P.max_iter >= 0 else nf // 2 + ri(0, nf, draw(g, 1, 2, 3))
         assert L.max_iter == mi and L.min_tabu == mi // 10 and L.max_tabu == (12 * mi) // 100
         child = orc.words_to_spins(list(L.post_tabu)[:W], N)
         assert np_energy(child)[0] == L.E_child <= np_energy(pre_tabu)[0]
         if fix:
             assert child[0] == 1 and pre_tabu[0] == 1
+        if skew:
+            assert is_skew(child) and is_skew(pre_tabu)
         bestE = min(bestE, L.E_child)
         if P.replace_policy == 0:
             slot = ri(0, K - 1, draw(g, 2, 2, 0))
@@ -373,6 +402,92 @@ def test_tabu_fixed_first_spin_replay(orc, N):
     max_iter = N // 2 + ((int(x) * (N + 1)) >> 32)
     E_rep, best_rep = replay_tabu(orc, s, N, tr, 7, 1, 2, max_iter, fix_first=True)
     assert E_rep == bestE and np.array_equal(orc.words_to_spins(best, N), best_rep)
+
+
+@pytest.mark.parametrize("N", [3, 5, 9, 15, 21])
+@pytest.mark.parametrize("fix", [False, True])
+def test_tabu_skew_replay(orc, N, fix):
+    """Skew-restricted tabu search (Sec. II.C): pairs of spins flipped together,
+    every step replayed by brute force; maxIter = floor(n/2) + randInt(0, n)."""
+    rng = np.random.default_rng(70 + N)
+    n = (N + 1) // 2
+    for trial in range(2):
+        s = rand_spins(rng, N)  # the oracle completes it from its free half
+        variant = orc.VARIANT_SKEW | (orc.VARIANT_FIX_FIRST_SPIN if fix else 0)
+        best, bestE, steps, tr = orc.tabu_run(orc.spins_to_words(s), N, 11, trial, 4, trace_cap=1000,
+                                              variant=variant)
+        x = orc.philox4x32_10([trial, 4, 1, 2], [11, 0])[3]
+        max_iter = n // 2 + ((int(x) * (n + 1)) >> 32)
+        assert steps == max_iter == len(tr)
+        E_rep, best_rep = replay_tabu(orc, s, N, tr, 11, trial, 4, max_iter, fix_first=fix, skew=True)
+        assert E_rep == bestE and np.array_equal(orc.words_to_spins(best, N), best_rep)
+        assert is_skew(best_rep)
+        C = np_energy(best_rep)[1]
+        assert all(C[k - 1] == 0 for k in range(1, N, 2))  # Eq. 4: odd lags vanish
+
+
+@pytest.mark.parametrize("variant", [4, 5, 6, 7])
+@pytest.mark.parametrize("N,K", [(7, 5), (25, 20), (71, 10)])
+def test_mts_skew_replay(orc, N, K, variant):
+    P = orc.make_params(N, K, max_generations=20, variant=variant)
+    assert P.p_mut_u32 == (1 << 32) // ((N + 1) // 2)
+    res, tr, gl = orc.mts_run(P, seed=6, instance=3, trace_cap=100000, genlog_cap=100)
+    replay_mts(orc, P, 6, 3, res, gl)
+    assert is_skew(orc.words_to_spins(res["seq"], N))
+
+
+def skew_optimum(N):
+    """min E over all 2^n skew-symmetric sequences (numpy enumeration)."""
+    n = (N + 1) // 2
+    codes = np.arange(1 << n, dtype=np.int64)
+    free = np.where((codes[:, None] >> np.arange(n)) & 1, 1, -1)
+    full = np.empty((len(codes), N), dtype=np.int64)
+    full[:, :n] = free
+    for i in range(1, n):
+        full[:, n + i - 1] = (-1) ** i * full[:, n - i - 1]
+    E = np.zeros(len(codes), dtype=np.int64)
+    for k in range(1, N):
+        E += np.sum(full[:, : N - k] * full[:, k:], axis=1) ** 2
+    return int(E.min())
+
+
+def test_skew_optimum_by_filtering():
+    """skew_optimum() equals the minimum over all 2^N sequences filtered by the
+    skew condition, for N = 13..19."""
+    for N in (13, 15, 17, 19):
+        codes = np.arange(1 << N, dtype=np.int64)
+        S = np.where((codes[:, None] >> np.arange(N)) & 1, 1, -1)
+        n = (N + 1) // 2
+        keep = np.ones(len(codes), dtype=bool)
+        for i in range(1, n):
+            keep &= S[:, n + i - 1] == (-1) ** i * S[:, n - i - 1]
+        S = S[keep]
+        assert len(S) == 1 << n
+        assert skew_optimum(N) == min(np_energy(x)[0] for x in S)
+
+
+@pytest.mark.parametrize("N", [13, 19, 25])
+def test_mts_skew_reaches_skew_optimum(orc, N):
+    """The restricted search reaches the exhaustive skew-symmetric optimum,
+    which is never below the exhaustive unrestricted optimum: equal at N = 13
+    (the skew-symmetric Barker length), strictly above it at N = 19 and 25,
+    odd lengths whose optima are not skew-symmetric (Sec. II.C)."""
+    E_skew = skew_optimum(N)
+    E_all = orc.bruteforce(N)[0]
+    if N == 13:
+        assert E_skew == E_all == 6
+    else:
+        assert E_skew > E_all
+    P = orc.make_params(N, 20, target_E=E_skew, max_generations=3000, variant=orc.VARIANT_SKEW)
+    res, _, _ = orc.mts_run(P, seed=2)
+    assert res["E"] == E_skew and res["status"] == orc.STATUS_REACHED
+
+
+def test_skew_variant_refuses_even_N(orc):
+    with pytest.raises(Exception):
+        orc.mts_run(orc.make_params(20, 5, max_generations=1, variant=orc.VARIANT_SKEW), 0)
+    with pytest.raises(Exception):
+        orc.tabu_run(orc.spins_to_words(np.ones(20, dtype=np.int64)), 20, 0, 0, variant=orc.VARIANT_SKEW)
 
 
 @pytest.mark.parametrize("N", [5, 12, 33, 66])
