@@ -36,7 +36,8 @@ SM_COUNT_GB300 = 152
 INT32_LANES_PER_SM = 128  # 4 SM sub-partitions x 32 lanes
 SM_MAX_MHZ_GB300 = 2070.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "mts_kernel_n64_traffic.json")
-KERNEL_SOURCES = ["tabu_core.cuh", "replica.cuh", "mts.cu", "labs_device.cuh", "kernels.h"]
+KERNEL_SOURCES = ["tabu_core.cuh", "tabu_skew.cuh", "replica.cuh", "mts_kernels.cuh", "mts.cu", "labs_device.cuh",
+                  "kernels.h"]
 
 
 def kernel_hash() -> str:
@@ -413,7 +414,7 @@ def tts_rows(torch, labs, Ns, targets, reps, cap, runs, stream, variant=0, repla
         P = labs.make_params(n, 100, target_E=target, max_steps=cap, glf=True, variant=variant,
                              replace_policy=replace_policy)
         labs.mts_launch(labs.make_params(n, 100, max_steps=1000, variant=variant), 0, 0, reps)
-        times, reached = [], 0
+        times, work, reached = [], [], 0
         for run in range(runs):
             flag = torch.zeros(1, dtype=torch.int32, device=stream.device)
             ms, out = timed_launch(torch, lambda: labs.mts_launch(P, 1000 + run, 0, reps, glf_flag=flag,
@@ -422,22 +423,24 @@ def tts_rows(torch, labs, Ns, targets, reps, cap, runs, stream, variant=0, repla
             ok = any(r["status"] == labs.RUN_REACHED for r in res)
             reached += ok
             times.append(ms / 1e3 if ok else float("inf"))
-        t = np.array(times)
+            work.append(sum(r["steps"] for r in res) if ok else float("inf"))  # tabu steps, all replicas
+        t, w = np.array(times), np.array(work)
         rows.append({"N": n, "target_E": target, "runs": runs, "reached": reached,
                      "p50_s": float(np.percentile(t, 50)), "p99_s": float(np.percentile(t, 99)),
                      "q1_s": float(np.percentile(t, 25)), "q3_s": float(np.percentile(t, 75)),
+                     "p50_steps": float(np.percentile(w, 50)),
                      "times_s": [round(x, 6) for x in times]})
         print(json.dumps({k: v for k, v in rows[-1].items() if k != "times_s"}), file=sys.stderr, flush=True)
     return rows
 
 
-def median_fit(rows):
+def median_fit(rows, key="p50_s"):
     import numpy as np
 
-    ok_rows = [r for r in rows if np.isfinite(r["p50_s"])]
+    ok_rows = [r for r in rows if np.isfinite(r[key])]
     if len(ok_rows) < 3:
         return None
-    return fit_exponential([r["N"] for r in ok_rows], [r["p50_s"] for r in ok_rows])
+    return fit_exponential([r["N"] for r in ok_rows], [r[key] for r in ok_rows])
 
 
 def run_tts(args) -> None:
@@ -526,6 +529,55 @@ def run_tts_ab(args) -> None:
                                    f"the global termination flag, K=100, cap {cap} steps per replica",
                        "runs_per_N": args.runs, "targets": kind},
             "policies": summary}), flush=True)
+
+
+def run_skew_ab(args) -> None:
+    """Unrestricted search against the search restricted to skew-symmetric
+    sequences (Sec. II.C), odd N = 17..45.  Both race to the exhaustive
+    skew-symmetric optimum (reachable by both); where the exhaustive optimum
+    over all sequences is known (N <= 31) the unrestricted search also races
+    to it (the restricted one reaches it only if it is skew-symmetric).  Per
+    N: median time and median tabu steps (all replicas) to target, and an
+    a * b^N fit of each median."""
+    torch, dev, pg, world, rank = gpu_context(args)
+    import paper_2504_00987_gb300 as labs
+
+    skew_opt = load_targets("skew_optimum_odd_n17_45")
+    all_opt = load_targets("optimum_n16_32")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    reps = args.replicas or sms * 8
+    cap = args.steps_per_replica or 2_000_000
+    stream = torch.cuda.current_stream()
+    Ns = [int(x) for x in args.tts_n.split(",")] if args.tts_n else sorted(skew_opt)
+    runs = args.runs
+    rows_u = tts_rows(torch, labs, Ns, skew_opt, reps, cap, runs, stream)
+    rows_s = tts_rows(torch, labs, Ns, skew_opt, reps, cap, runs, stream, variant=labs.VARIANT_SKEW)
+    Ns_all = [n for n in Ns if n in all_opt and all_opt[n] < skew_opt[n]]
+    rows_o = tts_rows(torch, labs, Ns_all, all_opt, reps, cap, runs, stream) if Ns_all else []
+    per_n = []
+    for u, k in zip(rows_u, rows_s):
+        n = u["N"]
+        o = next((x for x in rows_o if x["N"] == n), None)
+        per_n.append({
+            "N": n, "E_skew_opt": skew_opt[n], "E_opt": all_opt.get(n),
+            "unrestricted_to_skew_opt": {x: u[x] for x in ("reached", "p50_s", "q1_s", "q3_s", "p50_steps")},
+            "restricted_to_skew_opt": {x: k[x] for x in ("reached", "p50_s", "q1_s", "q3_s", "p50_steps")},
+            "p50_steps_ratio_restricted_vs_unrestricted": k["p50_steps"] / u["p50_steps"],
+            "unrestricted_to_opt": ({x: o[x] for x in ("reached", "p50_s", "p50_steps")} if o else None),
+        })
+    if rank == 0:
+        ratios = [r["p50_steps_ratio_restricted_vs_unrestricted"] for r in per_n]
+        print(json.dumps({
+            "metric": "tabu steps to the skew-symmetric optimum, restricted / unrestricted (geomean over N)",
+            "value": statistics.geometric_mean(ratios), "unit": "ratio", "n_gpus": world,
+            "higher_is_better": False, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"skew_ab: odd N={Ns}, {reps} replicas with the global termination flag, "
+                                   f"K=100, cap {cap} steps per replica", "runs_per_N": runs,
+                       "targets": "skew_optimum_odd_n17_45, optimum_n16_32"},
+            "fit_unrestricted_p50_steps": median_fit(rows_u, "p50_steps"),
+            "fit_restricted_p50_steps": median_fit(rows_s, "p50_steps"),
+            "fit_unrestricted_p50_s": median_fit(rows_u), "fit_restricted_p50_s": median_fit(rows_s),
+            "per_N": per_n}), flush=True)
 
 
 def run_batch(args) -> None:
@@ -710,8 +762,8 @@ def main() -> None:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--replicas", type=int, default=0, help="profiling only: override replicas")
     ap.add_argument("--steps-per-replica", type=int, default=0, help="profiling only: override budget")
-    ap.add_argument("--workload", choices=["replicas_n64", "sweep_n92_120", "tts", "tts_ab", "batch", "serve",
-                                           "skew"],
+    ap.add_argument("--workload", choices=["replicas_n64", "sweep_n92_120", "tts", "tts_ab", "skew_ab", "batch",
+                                           "serve", "skew"],
                     default="replicas_n64")
     ap.add_argument("--runs", type=int, default=50, help="tts: runs per N")
     ap.add_argument("--tts-n", default="", help="tts: comma-separated N (default: all; tts_ab: first five)")
@@ -731,6 +783,8 @@ def main() -> None:
         run_tts(args)
     elif args.workload == "tts_ab":
         run_tts_ab(args)
+    elif args.workload == "skew_ab":
+        run_skew_ab(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "serve":

@@ -60,6 +60,17 @@ extern "C" {
 #define LABS_VARIANT_FIX_FIRST_SPIN 2    /* s_1 = +1 throughout (Sec. II.B symmetry break):
                                             initial members with s_1 = -1 are complemented,
                                             s_1 is never mutated nor flipped by the tabu search */
+#define LABS_VARIANT_SKEW 4              /* odd N only: the search runs over skew-symmetric
+                                            sequences s_{n+i} = (-1)^i s_{n-i}, N = 2n-1
+                                            (Sec. II.C).  Sequences are completed from their
+                                            free half s_1..s_n; the crossover cut is
+                                            randInt(1, n-1); mutation (default rate 1/n) acts
+                                            on the free half; a tabu move flips a free spin
+                                            and its partner; maxIter = floor(n/2) +
+                                            randInt(0, n).  labs_mts_launch, labs_mts_run,
+                                            labs_mts_run_static and labs_tabu_run (which
+                                            completes each start from its free half) take
+                                            it; batches and the service refuse it. */
 
 /* Why a replica stopped. */
 #define LABS_RUN_BUDGET 0  /* generation or step budget used up */

@@ -139,6 +139,7 @@ def lib():
                 P(Result),
             ]
             L.orc_bruteforce.argtypes = [ctypes.c_int32, i32p, i64p, u64p]
+            L.orc_bruteforce_skew.argtypes = [ctypes.c_int32, i32p, i64p]
             L.orc_non_skew_pairs.argtypes = [u64p, ctypes.c_int32]
             L.orc_skew_deviation.argtypes = [u64p, ctypes.c_int32]
             L.orc_skew_deviation_mode.argtypes = [u64p, ctypes.c_int32, ctypes.c_int32]
@@ -303,6 +304,16 @@ def bruteforce(N: int):
         raise ValueError("bad arguments")
     return int(E[0]), int(n[0]), a.copy()
 
+
+
+def bruteforce_skew(N: int):
+    """Exhaustive minimum over the skew-symmetric sequences of odd N <= 45:
+    (E_min, number of minimisers)."""
+    E = np.zeros(1, dtype=np.int32)
+    n = np.zeros(1, dtype=np.int64)
+    if lib().orc_bruteforce_skew(N, _ptr(E, ctypes.c_int32), _ptr(n, ctypes.c_int64)) != 0:
+        raise ValueError("odd N in 3..45 only")
+    return int(E[0]), int(n[0])
 
 def non_skew_pairs(words, N: int) -> int:
     w = _words(words, N)

@@ -722,6 +722,30 @@ int32_t orc_bruteforce(int32_t N, int32_t* E_min, int64_t* n_min, uint64_t* argm
     return 0;
 }
 
+/* Exhaustive minimum of E over the skew-symmetric sequences of odd length N
+ * (Sec. II.C): every assignment of the n = (N+1)/2 free spins, completed
+ * by symmetrize() and scored from Eq. 2.  n_min counts the minimisers. */
+int32_t orc_bruteforce_skew(int32_t N, int32_t* E_min, int64_t* n_min) {
+    if (N < 3 || N > 45 || N % 2 == 0 || !E_min) return -1;
+    const int n = (N + 1) / 2;
+    int8_t s[ORC_MAX_N];
+    int64_t best = -1, count = 0;
+    for (uint64_t code = 0; code < ((uint64_t)1 << n); ++code) {
+        for (int i = 0; i < n; ++i) s[i] = ((code >> i) & 1) ? 1 : -1;
+        symmetrize(s, N);
+        const int64_t E = energy_spins(s, N, 0);
+        if (best < 0 || E < best) {
+            best = E;
+            count = 1;
+        } else if (E == best) {
+            ++count;
+        }
+    }
+    *E_min = (int32_t)best;
+    if (n_min) *n_min = count;
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Appendix A: deviation from skew-symmetry.                                 */
 /* Eq. 5: for odd length L = 2n - 1, n_non-skew counts i = 1..n-1 with      */

@@ -35,4 +35,7 @@ from ._native import (  # noqa: F401
     RUN_BUDGET,
     RUN_REACHED,
     RUN_STOPPED,
+    VARIANT_FIX_FIRST_SPIN,
+    VARIANT_SKEW,
+    VARIANT_UNIFORM_CROSSOVER,
 )

@@ -44,6 +44,7 @@ EXPORTED = [
 STATIC_MAX_REPLICAS = 4096
 VARIANT_UNIFORM_CROSSOVER = 1
 VARIANT_FIX_FIRST_SPIN = 2
+VARIANT_SKEW = 4
 ORDER_LPT = 0
 ORDER_GIVEN = 1
 

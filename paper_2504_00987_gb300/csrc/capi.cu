@@ -88,14 +88,23 @@ int32_t check_run(int32_t N, int32_t K, int32_t replace_policy, int32_t target_E
     return LABS_OK;
 }
 
-int32_t check_variant(int32_t variant, const char* who) {
-    if (variant & ~(LABS_VARIANT_UNIFORM_CROSSOVER | LABS_VARIANT_FIX_FIRST_SPIN))
+int32_t check_variant(int32_t variant, int32_t N, bool skew_allowed, const char* who) {
+    if (variant & ~(LABS_VARIANT_UNIFORM_CROSSOVER | LABS_VARIANT_FIX_FIRST_SPIN | LABS_VARIANT_SKEW))
         return fail(LABS_EINVAL, "%s: unknown variant flags 0x%x", who, variant);
+    if (variant & LABS_VARIANT_SKEW) {
+        if (!skew_allowed)
+            return fail(LABS_EINVAL,
+                        "%s: LABS_VARIANT_SKEW runs through labs_mts_launch/run/run_static and "
+                        "labs_tabu_run only", who);
+        if (N % 2 == 0) return fail(LABS_EINVAL, "%s: LABS_VARIANT_SKEW needs odd N (N=%d)", who, N);
+    }
     return LABS_OK;
 }
 
-uint32_t default_p_mut(int32_t N, uint32_t p_mut_u32) {
-    return p_mut_u32 != 0 ? p_mut_u32 : static_cast<uint32_t>((1ull << 32) / N);
+uint32_t default_p_mut(int32_t N, uint32_t p_mut_u32, int32_t variant) {
+    if (p_mut_u32 != 0) return p_mut_u32;
+    const int32_t free_spins = (variant & LABS_VARIANT_SKEW) ? (N + 1) / 2 : N;  // 1 / (spins mutated)
+    return static_cast<uint32_t>((1ull << 32) / free_spins);
 }
 
 int sm_count() {
@@ -137,7 +146,7 @@ int32_t make_mts_args(const labs_params* P, uint64_t seed, uint64_t first_instan
         return fail(LABS_EINVAL, "too many replicas for one launch");
     if (P->trace_cap < 0) return fail(LABS_EINVAL, "trace_cap < 0");
     if (P->d_trace != nullptr) LABS_TRY(check_dev(P->d_trace, 16, "d_trace", false));
-    LABS_TRY(check_variant(P->variant, "params"));
+    LABS_TRY(check_variant(P->variant, P->N, true, "params"));
     const size_t per_warp = lgpu::mts_smem_per_warp(P->N, P->K);
     if (per_warp * lgpu::kWarpsPerBlock > 227u * 1024u)
         return fail(LABS_EINVAL, "population does not fit in shared memory (N=%d, K=%d)", P->N, P->K);
@@ -145,7 +154,7 @@ int32_t make_mts_args(const labs_params* P, uint64_t seed, uint64_t first_instan
     a->N = P->N;
     a->K = P->K;
     a->p_comb_u32 = P->p_comb_u32;
-    a->p_mut_u32 = default_p_mut(P->N, P->p_mut_u32);
+    a->p_mut_u32 = default_p_mut(P->N, P->p_mut_u32, P->variant);
     a->replace_policy = P->replace_policy;
     a->target_E = P->target_E;
     a->max_generations = P->max_generations;
@@ -195,7 +204,7 @@ int32_t labs_tabu_run(const uint64_t* d_start, int32_t N, int64_t B, uint64_t se
     if (opts->max_iter < -1 || opts->max_iter > (1 << 20))
         return fail(LABS_EINVAL, "max_iter=%d outside -1..2^20", opts->max_iter);
     if (opts->trace_cap < 0) return fail(LABS_EINVAL, "trace_cap < 0");
-    LABS_TRY(check_variant(opts->variant, "opts"));
+    LABS_TRY(check_variant(opts->variant, N, true, "opts"));
     if (opts->first_instance + static_cast<uint64_t>(B) > 0x100000000ull)
         return fail(LABS_EINVAL, "instances beyond 2^32 - 1");
     if (B == 0) return ok();

@@ -53,7 +53,7 @@ int32_t validate_instances(const labs_instance* h, int64_t n) {
         snprintf(who, sizeof who, "instance %lld", static_cast<long long>(i));
         LABS_TRY(check_run(x.N, x.K, x.replace_policy, x.target_E, x.max_generations, x.max_steps,
                            x.max_iter, x.instance, 1, who));
-        LABS_TRY(check_variant(x.variant, who));
+        LABS_TRY(check_variant(x.variant, x.N, false, who));
     }
     return LABS_OK;
 }
@@ -126,7 +126,7 @@ cudaError_t upload(const std::vector<labs_instance>& h, const std::vector<int32_
     std::vector<labs_instance> q(n);
     for (size_t i = 0; i < n; ++i) {
         q[i] = h[static_cast<size_t>(ord[i])];
-        q[i].p_mut_u32 = default_p_mut(q[i].N, q[i].p_mut_u32);
+        q[i].p_mut_u32 = default_p_mut(q[i].N, q[i].p_mut_u32, q[i].variant);
     }
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d->inst), sizeof(labs_instance) * std::max<size_t>(n, 1));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&d->order), sizeof(int32_t) * std::max<size_t>(n, 1));

@@ -178,7 +178,7 @@ void scheduler(labs_server* s) {
                 s->stats.running++;
                 s->stats.pending--;
                 s->h_cfg[slot] = t.req;
-                s->h_cfg[slot].p_mut_u32 = default_p_mut(t.req.N, t.req.p_mut_u32);
+                s->h_cfg[slot].p_mut_u32 = default_p_mut(t.req.N, t.req.p_mut_u32, t.req.variant);
                 fresh.push_back(slot);
             }
             active.clear();
@@ -347,7 +347,7 @@ int32_t labs_serve_submit(labs_server* s, const labs_request* req, uint64_t* tic
     if (s == nullptr || req == nullptr || ticket == nullptr) return fail(LABS_EINVAL, "NULL argument");
     LABS_TRY(check_run(req->N, req->K, req->replace_policy, req->target_E, req->max_generations,
                        req->max_steps, req->max_iter, req->instance, 1, "request"));
-    LABS_TRY(check_variant(req->variant, "request"));
+    LABS_TRY(check_variant(req->variant, req->N, false, "request"));
     if (req->N > s->opts.max_N || req->K > s->opts.max_K)
         return fail(LABS_EINVAL, "request N=%d K=%d beyond the server's max_N=%d max_K=%d", req->N, req->K,
                     s->opts.max_N, s->opts.max_K);

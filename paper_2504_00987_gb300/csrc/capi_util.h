@@ -21,8 +21,10 @@ int32_t check_N(int32_t N);
 int32_t check_run(int32_t N, int32_t K, int32_t replace_policy, int32_t target_E,
                   int64_t max_generations, int64_t max_steps, int32_t max_iter, uint64_t first_instance,
                   int64_t count, const char* who);
-int32_t check_variant(int32_t variant, const char* who);
-uint32_t default_p_mut(int32_t N, uint32_t p_mut_u32);
+// Unknown flags, and LABS_VARIANT_SKEW with even N or where it is not served.
+int32_t check_variant(int32_t variant, int32_t N, bool skew_allowed, const char* who);
+// The given threshold, or floor(2^32 / spins mutated) if 0.
+uint32_t default_p_mut(int32_t N, uint32_t p_mut_u32, int32_t variant);
 int sm_count();
 void fill_host_result(const labs_device_result& d, int32_t N, uint64_t instance, double seconds,
                       labs_result* o);

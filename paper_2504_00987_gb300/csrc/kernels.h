@@ -83,6 +83,8 @@ cudaError_t launch_batch(const BatchArgs& a, int nwmax, int blocks, int warps_pe
                          cudaStream_t stream);
 cudaError_t launch_mts(const MtsArgs& a, cudaStream_t stream);
 cudaError_t launch_tabu(const TabuArgs& a, cudaStream_t stream);
+cudaError_t launch_mts_skew(const MtsArgs& a, cudaStream_t stream);   // mts_skew.cu
+cudaError_t launch_tabu_skew(const TabuArgs& a, cudaStream_t stream);
 cudaError_t launch_energy(const uint64_t* d_seqs, int N, int64_t B, int32_t* d_E, int32_t* d_C,
                           cudaStream_t stream);
 

@@ -122,4 +122,32 @@ __device__ __forceinline__ void reverse_bits(const uint32_t (&in)[NW], uint32_t 
     for (int w = 0; w < NW; ++w) out[w] = __brev(in[NW - 1 - w]);
 }
 
+// Bit i of an NW-word vector (0 <= i < 32*NW; i may differ between lanes).
+template <int NW>
+__device__ __forceinline__ uint32_t get_bit(const uint32_t (&v)[NW], int i) {
+    const int wi = i >> 5;
+    uint32_t x = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) x = (w == wi) ? v[w] : x;
+    return (x >> (i & 31)) & 1u;
+}
+
+// Skew-symmetric completion of an odd-length sequence (Sec. II.C): with
+// centre c = (N-1)/2, s_{c+i} = (-1)^i s_{c-i} for i = 1..c, i.e.
+// b_{c+i} = b_{c-i} xor (i odd).  Bits [0, c] are kept, bits >= N cleared.
+template <int NW>
+__device__ __forceinline__ void skew_complete(uint32_t (&B)[NW], int N) {
+    constexpr int NB = 32 * NW;
+    const int c = (N - 1) >> 1;
+    uint32_t RL[NW], RN[NW];
+    reverse_bits<NW>(B, RL);
+    shr_uniform<NW>(RL, NB - N, RN);                            // bit m of RN = b_{N-1-m}
+    const uint32_t alt = (c & 1) ? 0x55555555u : 0xAAAAAAAAu;  // bit m set iff m - c odd
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const uint32_t keep = word_lowmask(w, c + 1);
+        B[w] = (B[w] & keep) | ((RN[w] ^ alt) & word_lowmask(w, N) & ~keep);
+    }
+}
+
 }  // namespace lgpu

@@ -1,0 +1,137 @@
+// mts_kernels.cuh -- Memetic-Tabu (Algorithm 1 / Algorithm 3) and batched
+// tabu search (Algorithm 2 / Algorithm 4) kernels, templated on the word
+// count, tracing and the skew-symmetric restriction (Sec. II.C).  One warp
+// runs one replica: its population lives in the warp's slice of shared
+// memory (K packed sequences and their energies), its pivot, correlations
+// and tabu list in registers.  Replicas never synchronise with each other;
+// the only cross-replica state is the optional global termination flag.
+// mts.cu instantiates the unrestricted kernels, mts_skew.cu the restricted
+// ones, so each translation unit compiles one family.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "replica.cuh"
+
+namespace lgpu {
+
+template <int NW, bool TRACE, bool SKEW>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) mts_kernel(const MtsArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + warp;
+    if (r >= a.replicas) return;
+
+    uint32_t* pop = reinterpret_cast<uint32_t*>(smem + static_cast<size_t>(warp) * a.smem_per_warp);
+    int32_t* popE = reinterpret_cast<int32_t*>(pop + a.K * NW);
+    int32_t* Cs = popE + a.K;
+    ReplicaCfg cfg;
+    cfg.N = a.N;
+    cfg.K = a.K;
+    cfg.p_comb_u32 = a.p_comb_u32;
+    cfg.p_mut_u32 = a.p_mut_u32;
+    cfg.replace_policy = a.replace_policy;
+    cfg.target_E = a.target_E;
+    cfg.max_generations = a.max_generations;
+    cfg.max_steps = a.max_steps;
+    cfg.max_iter = a.max_iter;
+    cfg.variant = a.variant;
+    cfg.inst = static_cast<uint32_t>(a.first_instance + static_cast<uint64_t>(r));
+    cfg.key = philox_key(a.seed);
+    int4* trace = a.d_trace ? a.d_trace + r * a.trace_cap : nullptr;
+    replica_run<NW, TRACE, SKEW>(cfg, pop, popE, Cs, trace, a.trace_cap, a.d_glf, a.d_out + r, lane);
+}
+
+template <int NW, bool TRACE, bool SKEW>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) tabu_kernel(const TabuArgs a) {
+    __shared__ int32_t Cs_all[kWarpsPerBlock][32 * NW];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t b = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + warp;
+    if (b >= a.B) return;
+    const int N = a.N;
+    const uint2 key = philox_key(a.seed);
+    const uint32_t inst = static_cast<uint32_t>(a.first_instance + static_cast<uint64_t>(b));
+    uint32_t seq[NW];
+    load_seq<NW>(reinterpret_cast<const uint32_t*>(a.d_start) + b * NW, seq);
+#pragma unroll
+    for (int w = 0; w < NW; ++w) seq[w] &= word_lowmask(w, N);  // bits >= N are ignored
+    if constexpr (SKEW) skew_complete<NW>(seq, N);              // the free half decides
+    const int nmov = SKEW ? (N + 1) / 2 : N;
+    int max_iter = a.max_iter;
+    if (max_iter < 0) {
+        const uint4 d = draw4(key, inst, a.generation, 1u, kPurposeGen);
+        max_iter = nmov / 2 + rand_int(0, nmov, d.w);
+    }
+    int4* trace = a.d_trace ? a.d_trace + b * a.trace_cap : nullptr;
+    int64_t trace_len = 0;
+    const bool fix = (a.variant & LABS_VARIANT_FIX_FIRST_SPIN) != 0;
+    TabuOut to;
+    if constexpr (SKEW) {
+        to = fix ? tabu_search_skew<NW, TRACE, true>(seq, N, key, inst, a.generation, max_iter, -1,
+                                                     Cs_all[warp], trace, a.trace_cap, trace_len, lane)
+                 : tabu_search_skew<NW, TRACE, false>(seq, N, key, inst, a.generation, max_iter, -1,
+                                                      Cs_all[warp], trace, a.trace_cap, trace_len, lane);
+    } else {
+        to = fix ? tabu_search<NW, TRACE, true>(seq, N, key, inst, a.generation, max_iter, -1,
+                                                Cs_all[warp], trace, a.trace_cap, trace_len, lane)
+                 : tabu_search<NW, TRACE, false>(seq, N, key, inst, a.generation, max_iter, -1,
+                                                 Cs_all[warp], trace, a.trace_cap, trace_len, lane);
+    }
+    if (lane < NW) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) v = (lane == w) ? seq[w] : v;
+        reinterpret_cast<uint32_t*>(a.d_best)[b * NW + lane] = v;
+    }
+    if (lane == 0) {
+        a.d_bestE[b] = to.E_best;
+        if (a.d_steps) a.d_steps[b] = to.steps;
+    }
+}
+
+template <int NW, bool TRACE, bool SKEW>
+cudaError_t launch_mts_t(const MtsArgs& a, cudaStream_t stream) {
+    const size_t smem = a.smem_per_warp * kWarpsPerBlock;
+    cudaError_t e = cudaFuncSetAttribute(mts_kernel<NW, TRACE, SKEW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (a.replicas + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    mts_kernel<NW, TRACE, SKEW><<<static_cast<unsigned>(blocks), kWarpsPerBlock * 32, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool SKEW>
+cudaError_t launch_mts_family(const MtsArgs& a, cudaStream_t stream) {
+    const bool tr = a.d_trace != nullptr;
+    switch ((a.N + 63) / 64) {
+        case 1: return tr ? launch_mts_t<2, true, SKEW>(a, stream) : launch_mts_t<2, false, SKEW>(a, stream);
+        case 2: return tr ? launch_mts_t<4, true, SKEW>(a, stream) : launch_mts_t<4, false, SKEW>(a, stream);
+        case 3: return tr ? launch_mts_t<6, true, SKEW>(a, stream) : launch_mts_t<6, false, SKEW>(a, stream);
+        default: return tr ? launch_mts_t<8, true, SKEW>(a, stream) : launch_mts_t<8, false, SKEW>(a, stream);
+    }
+}
+
+template <int NW, bool SKEW>
+cudaError_t launch_tabu_w(const TabuArgs& a, cudaStream_t stream) {
+    const int64_t blocks = (a.B + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (a.d_trace)
+        tabu_kernel<NW, true, SKEW><<<static_cast<unsigned>(blocks), kWarpsPerBlock * 32, 0, stream>>>(a);
+    else
+        tabu_kernel<NW, false, SKEW><<<static_cast<unsigned>(blocks), kWarpsPerBlock * 32, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool SKEW>
+cudaError_t launch_tabu_family(const TabuArgs& a, cudaStream_t stream) {
+    switch ((a.N + 63) / 64) {
+        case 1: return launch_tabu_w<2, SKEW>(a, stream);
+        case 2: return launch_tabu_w<4, SKEW>(a, stream);
+        case 3: return launch_tabu_w<6, SKEW>(a, stream);
+        default: return launch_tabu_w<8, SKEW>(a, stream);
+    }
+}
+
+}  // namespace lgpu

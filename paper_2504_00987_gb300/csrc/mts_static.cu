@@ -77,7 +77,7 @@ extern "C" int32_t labs_mts_run_static(const labs_params* P, uint64_t seed, uint
         return fail(LABS_EINVAL, "replicas=%lld exceeds the static scratch maximum of %lld",
                     static_cast<long long>(replicas), static_cast<long long>(kMaxReplicas));
     if (P->trace_cap < 0) return fail(LABS_EINVAL, "trace_cap < 0");
-    LABS_TRY(check_variant(P->variant, "params"));
+    LABS_TRY(check_variant(P->variant, P->N, true, "params"));
     if (P->d_trace != nullptr) LABS_TRY(check_dev(P->d_trace, 16, "d_trace", false));
     const size_t per_warp = lgpu::mts_smem_per_warp(P->N, P->K);
     if (per_warp * lgpu::kWarpsPerBlock > 227u * 1024u)
@@ -94,7 +94,7 @@ extern "C" int32_t labs_mts_run_static(const labs_params* P, uint64_t seed, uint
     a.N = P->N;
     a.K = P->K;
     a.p_comb_u32 = P->p_comb_u32;
-    a.p_mut_u32 = default_p_mut(P->N, P->p_mut_u32);
+    a.p_mut_u32 = default_p_mut(P->N, P->p_mut_u32, P->variant);
     a.replace_policy = P->replace_policy;
     a.target_E = P->target_E;
     a.max_generations = P->max_generations;

@@ -6,9 +6,15 @@
 // registers.  The functions are split at generation boundaries so a replica
 // can also be suspended and resumed there (the state between generations
 // is the population, the best sequence and the counters).
+//
+// SKEW (compile time; odd N): every sequence is skew-symmetric (Sec. II.C).
+// Members and children are completed from their free half b_0..b_c, the
+// cut is randInt(1, n-1) with n = c + 1, mutation acts on the free half,
+// maxIter = floor(n/2) + randInt(0, n), and the tabu search moves pairs.
 #pragma once
 
 #include "tabu_core.cuh"
+#include "tabu_skew.cuh"
 
 namespace lgpu {
 
@@ -84,7 +90,7 @@ __device__ __forceinline__ int tournament(const int32_t* __restrict__ popE, int 
 
 // population <- K random sequences (word w of member p from Philox
 // (inst, p, w/2, INIT)); bestSeq <- the lowest energy, lowest index on ties.
-template <int NW>
+template <int NW, bool SKEW = false>
 __device__ void replica_init(const ReplicaCfg& a, uint32_t* __restrict__ pop,
                              int32_t* __restrict__ popE, ReplicaState<NW>& st, int lane) {
     const int N = a.N, K = a.K;
@@ -95,6 +101,16 @@ __device__ void replica_init(const ReplicaCfg& a, uint32_t* __restrict__ pop,
         pop[p * NW + 2 * w64 + 1] = d.y & word_lowmask(2 * w64 + 1, N);
     }
     __syncwarp();
+    if constexpr (SKEW) {
+        for (int p = lane; p < K; p += 32) {
+            uint32_t B[NW];
+            load_seq<NW>(pop + p * NW, B);
+            skew_complete<NW>(B, N);
+#pragma unroll
+            for (int w = 0; w < NW; ++w) pop[p * NW + w] = B[w];
+        }
+        __syncwarp();
+    }
     if (a.variant & LABS_VARIANT_FIX_FIRST_SPIN) {  // complement members with s_1 = -1 (E unchanged)
         for (int p = lane; p < K; p += 32)
             if ((pop[p * NW] & 1u) == 0u)
@@ -145,7 +161,7 @@ __device__ __forceinline__ bool replica_should_stop(const ReplicaCfg& a, Replica
 }
 
 // One generation g = st.g.  Returns the tabu steps it took.
-template <int NW, bool TRACE = false>
+template <int NW, bool TRACE = false, bool SKEW = false>
 __device__ int64_t replica_generation(const ReplicaCfg& a, ReplicaState<NW>& st,
                                       uint32_t* __restrict__ pop, int32_t* __restrict__ popE,
                                       int32_t* __restrict__ Cs, int4* __restrict__ trace,
@@ -172,7 +188,7 @@ __device__ int64_t replica_generation(const ReplicaCfg& a, ReplicaState<NW>& st,
 #pragma unroll
             for (int w = 0; w < NW; ++w) child[w] = (pop[p1 * NW + w] & ~m2[w]) | (pop[p2 * NW + w] & m2[w]);
         } else {
-            const int cut = rand_int(1, N - 1, ucut);
+            const int cut = rand_int(1, (SKEW ? (N + 1) / 2 : N) - 1, ucut);
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
                 const uint32_t lm = word_lowmask(w, cut);
@@ -189,16 +205,27 @@ __device__ int64_t replica_generation(const ReplicaCfg& a, ReplicaState<NW>& st,
         if (a.variant & LABS_VARIANT_FIX_FIRST_SPIN) mm[0] &= ~1u;
 #pragma unroll
         for (int w = 0; w < NW; ++w) child[w] ^= mm[w];
+        // (bits above the free half are rewritten by the completion)
+        if constexpr (SKEW) skew_complete<NW>(child, N);
     }
     // child <- Tabu-Search(child)
-    const int max_iter = a.max_iter >= 0 ? a.max_iter : N / 2 + rand_int(0, N, uiter);
+    const int nmov = SKEW ? (N + 1) / 2 : N;  // tabu moves
+    const int max_iter = a.max_iter >= 0 ? a.max_iter : nmov / 2 + rand_int(0, nmov, uiter);
     const int64_t budget = a.max_steps >= 0 ? a.max_steps - st.steps : -1;
-    const TabuOut to =
-        (a.variant & LABS_VARIANT_FIX_FIRST_SPIN)
-            ? tabu_search<NW, TRACE, true>(child, N, a.key, a.inst, gg, max_iter, budget, Cs, trace,
-                                           trace_cap, trace_len, lane)
-            : tabu_search<NW, TRACE, false>(child, N, a.key, a.inst, gg, max_iter, budget, Cs, trace,
-                                            trace_cap, trace_len, lane);
+    TabuOut to;
+    if constexpr (SKEW) {
+        to = (a.variant & LABS_VARIANT_FIX_FIRST_SPIN)
+                 ? tabu_search_skew<NW, TRACE, true>(child, N, a.key, a.inst, gg, max_iter, budget, Cs,
+                                                     trace, trace_cap, trace_len, lane)
+                 : tabu_search_skew<NW, TRACE, false>(child, N, a.key, a.inst, gg, max_iter, budget, Cs,
+                                                      trace, trace_cap, trace_len, lane);
+    } else {
+        to = (a.variant & LABS_VARIANT_FIX_FIRST_SPIN)
+                 ? tabu_search<NW, TRACE, true>(child, N, a.key, a.inst, gg, max_iter, budget, Cs, trace,
+                                                trace_cap, trace_len, lane)
+                 : tabu_search<NW, TRACE, false>(child, N, a.key, a.inst, gg, max_iter, budget, Cs, trace,
+                                                 trace_cap, trace_len, lane);
+    }
     st.steps += to.steps;
     if (to.E_best < st.E_best) {
         st.E_best = to.E_best;
@@ -255,15 +282,15 @@ __device__ __forceinline__ void replica_store_result(const ReplicaState<NW>& st,
 }
 
 // A whole replica from scratch to its stop condition.
-template <int NW, bool TRACE = false>
+template <int NW, bool TRACE = false, bool SKEW = false>
 __device__ __forceinline__ void replica_run(const ReplicaCfg& a, uint32_t* pop, int32_t* popE,
                                             int32_t* Cs, int4* trace, int64_t trace_cap,
                                             uint32_t* glf, labs_device_result* out, int lane) {
     ReplicaState<NW> st;
     int64_t trace_len = 0;
-    replica_init<NW>(a, pop, popE, st, lane);
+    replica_init<NW, SKEW>(a, pop, popE, st, lane);
     while (!replica_should_stop<NW>(a, st, glf))
-        replica_generation<NW, TRACE>(a, st, pop, popE, Cs, trace, trace_cap, trace_len, glf, lane);
+        replica_generation<NW, TRACE, SKEW>(a, st, pop, popE, Cs, trace, trace_cap, trace_len, glf, lane);
     replica_store_result<NW>(st, trace_len, out, lane);
 }
 

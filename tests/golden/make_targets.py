@@ -13,8 +13,11 @@ Two sets, each a fixed amount of oracle work so the file is reproducible
                    of one core ("the oracle's 10 s best").
   optimum_n16_32 -- for N = 16..32: the exact minimum of E over all 2^N
                    sequences (the oracle's exhaustive search).
+  skew_optimum_odd_n17_45 -- for odd N = 17..45: the exact minimum of E over
+                   the 2^((N+1)/2) skew-symmetric sequences (Sec. II.C; the
+                   oracle's exhaustive search over the free half).
 
-Usage:  python tests/golden/make_targets.py [--only sweep|serve] [--threads T]
+Usage:  python tests/golden/make_targets.py [--only sweep|serve|optimum|skew] [--threads T]
 """
 from __future__ import annotations
 
@@ -48,7 +51,7 @@ def run_one(N: int, instance: int, steps: int) -> int:
 
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--only", choices=["sweep", "serve", "optimum"], default=None)
+    ap.add_argument("--only", choices=["sweep", "serve", "optimum", "skew"], default=None)
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
     args = ap.parse_args()
     oracle.build()
@@ -76,6 +79,12 @@ def main() -> None:
             data["optimum_n16_32"] = {
                 "targets": {str(N): {"E": E, "minimisers": n} for N, (E, n, _) in zip(Ns, opts)}}
             print(f"optimum: {len(Ns)} exhaustive minima ({time.time() - t0:.0f}s)", flush=True)
+        if args.only in (None, "skew"):
+            Ns = list(range(17, 46, 2))
+            opts = list(ex.map(oracle.bruteforce_skew, Ns))
+            data["skew_optimum_odd_n17_45"] = {
+                "targets": {str(N): {"E": E, "minimisers": n} for N, (E, n) in zip(Ns, opts)}}
+            print(f"skew: {len(Ns)} exhaustive skew-symmetric minima ({time.time() - t0:.0f}s)", flush=True)
     with open(OUT, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)
     print("wrote", OUT)

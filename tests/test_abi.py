@@ -69,10 +69,13 @@ def test_argument_errors_without_gpu(lib):
     P.replace_policy = 0
     assert lib.labs_mts_run(ctypes.byref(P), 0, 2**32 - 1, 2, res, None) == nat.LABS_EINVAL
     assert lib.labs_mts_run(ctypes.byref(P), 0, 0, 0, res, None) == nat.LABS_OK  # no replicas
-    P.variant = 4  # no such flag
+    P.variant = 8  # no such flag
     assert lib.labs_mts_run(ctypes.byref(P), 0, 0, 1, res, None) == nat.LABS_EINVAL
     assert b"variant" in lib.labs_last_error()
     assert lib.labs_mts_run_static(ctypes.byref(P), 0, 0, 1, res, None) == nat.LABS_EINVAL
+    P.variant = nat.VARIANT_SKEW  # N = 64 is even
+    assert lib.labs_mts_run(ctypes.byref(P), 0, 0, 1, res, None) == nat.LABS_EINVAL
+    assert b"odd N" in lib.labs_last_error()
     P.variant = 0
     opts = nat.TabuOpts(-2, 0, 0, 0, 0, 0)
     assert lib.labs_tabu_run(None, 64, 1, 0, ctypes.byref(opts), None, None, None, None, None) == nat.LABS_EINVAL
@@ -109,7 +112,10 @@ def test_batch_argument_errors_without_gpu(lib):
     arr[1].max_steps, arr[1].variant = 10, 16
     assert lib.labs_autotune(arr, 2, None, ctypes.byref(m)) == nat.LABS_EINVAL
     assert b"variant" in lib.labs_last_error()
-    arr[1].max_steps, arr[1].variant = -1, 0
+    arr[1].N, arr[1].variant = 63, nat.VARIANT_SKEW  # skew-symmetric runs are not batched
+    assert lib.labs_autotune(arr, 2, None, ctypes.byref(m)) == nat.LABS_EINVAL
+    assert b"SKEW" in lib.labs_last_error()
+    arr[1].N, arr[1].max_steps, arr[1].variant = 64, -1, 0
     h = ctypes.c_void_p()
     bad_map = nat.Mapping(3, 1, 0, 0)
     arr[1].max_steps = 10

@@ -1,8 +1,9 @@
 """GPU parity of the Algorithm 1 variants (uniform crossover; s_1 fixed to +1
-as the symmetry break of Sec. II.B) against the oracle: every tabu step,
-the final sequences and counters, through labs_tabu_run, labs_mts_launch,
-the batched launch and the solve service.  All exact integer work, so
-every comparison is bit-exact."""
+as the symmetry break of Sec. II.B; the search restricted to skew-symmetric
+sequences of Sec. II.C) against the oracle: every tabu step, the final
+sequences and counters, through labs_tabu_run, labs_mts_launch, the
+batched launch and the solve service.  All exact integer work, so every
+comparison is bit-exact."""
 import numpy as np
 import pytest
 
@@ -10,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-UNIFORM, FIX = 1, 2
+UNIFORM, FIX, SKEW = 1, 2, 4
 
 
 @pytest.fixture(scope="module")
@@ -140,6 +141,90 @@ def test_unknown_variant_flags_rejected(labs):
     from paper_2504_00987_gb300 import _native as nat
 
     with pytest.raises(nat.LabsError):
-        labs.mts_launch(labs.make_params(40, 10, max_generations=1, variant=4), 0, 0, 1)
+        labs.mts_launch(labs.make_params(40, 10, max_generations=1, variant=8), 0, 0, 1)
     with pytest.raises(nat.LabsError):
         labs.tabu_run(dev_seqs(np.zeros((1, 1), dtype=np.uint64)), 40, 0, variant=8)
+
+
+def is_skew_words(words, N):
+    """Sec. II.C on packed bits: b_{c+i} = b_{c-i} xor (i odd), c = (N-1)/2."""
+    v = sum(int(w) << (64 * k) for k, w in enumerate(words))
+    b = [(v >> i) & 1 for i in range(N)]
+    c = (N - 1) // 2
+    return all(b[c + i] == b[c - i] ^ (i & 1) for i in range(1, c + 1))
+
+
+@pytest.mark.parametrize("N", [3, 5, 31, 33, 63, 65, 101, 127, 129, 191, 193, 255])
+@pytest.mark.parametrize("fix", [False, True])
+def test_tabu_skew(labs, wl, orc, N, fix):
+    """Pair moves of the skew-restricted search: every step's move and energy."""
+    B = 37
+    variant = SKEW | (FIX if fix else 0)
+    starts = wl.random_sequences(N, B, seed=500 + N)
+    cap = N + 2
+    out = labs.tabu_run(dev_seqs(starts), N, seed=21, generation=3, first_instance=9, trace_cap=cap,
+                        variant=variant)
+    best = out["best"].cpu().numpy().view(np.uint64)
+    bestE, steps, trace = out["bestE"].cpu().numpy(), out["steps"].cpu().numpy(), out["trace"].cpu().numpy()
+    for b in range(B):
+        ob, oE, osteps, otr = orc.tabu_run(starts[b], N, 21, 9 + b, 3, trace_cap=cap, variant=variant)
+        assert steps[b] == osteps and bestE[b] == oE
+        assert np.array_equal(best[b], ob)
+        assert np.array_equal(trace[b, :osteps], otr)
+        assert is_skew_words(best[b], N)
+
+
+@pytest.mark.parametrize("variant", [SKEW, SKEW | UNIFORM, SKEW | FIX, SKEW | UNIFORM | FIX])
+@pytest.mark.parametrize("N,K", [(3, 2), (7, 5), (25, 100), (63, 20), (65, 7), (101, 50), (129, 20),
+                                 (201, 10), (255, 3)])
+def test_mts_skew(labs, orc, variant, N, K):
+    R, G = 6, 6
+    cap = G * (3 * N // 4 + 3) + G
+    kw = dict(max_generations=G, variant=variant, replace_policy=N % 2 if K > 5 else 0)
+    res, tr = run_gpu_mts(labs, N, K, 43, R, cap, **kw)
+    for r, g in enumerate(res):
+        o, otr, _ = orc.mts_run(orc.make_params(N, K, **kw), 43, r, trace_cap=cap)
+        assert (g["E"], g["status"], g["generations"], g["steps"]) == \
+            (o["E"], o["status"], o["generations"], o["steps"])
+        assert g["seq"] == [int(x) for x in o["seq"]]
+        assert g["trace_len"] == len(otr)
+        assert np.array_equal(tr[r, : len(otr)], otr)
+        assert is_skew_words(g["seq"], N)
+
+
+def test_mts_skew_budget_target_and_entry_points(labs, orc):
+    """A step budget that ends a search mid-way, a target, and the blocking
+    and allocation-free entry points, all against the oracle."""
+    N, K, R = 77, 30, 8
+    res, tr = run_gpu_mts(labs, N, K, 5, R, 3000, max_steps=1111, variant=SKEW)
+    for r, g in enumerate(res):
+        o, otr, _ = orc.mts_run(orc.make_params(N, K, max_steps=1111, variant=SKEW), 5, r, trace_cap=3000)
+        assert g["steps"] == o["steps"] == 1111 and g["E"] == o["E"]
+        assert np.array_equal(tr[r, : len(otr)], otr)
+    target = min(g["E"] for g in res) + 40
+    P = labs.make_params(N, K, target_E=target, max_generations=500, variant=SKEW | FIX)
+    a = labs.mts_run(P, 2, 0, 4)
+    for r, g in enumerate(a):
+        o, _, _ = orc.mts_run(orc.make_params(N, K, target_E=target, max_generations=500, variant=SKEW | FIX),
+                              2, r)
+        assert (g["E"], g["seq"], g["steps"], g["status"]) == (o["E"], [int(x) for x in o["seq"]], o["steps"],
+                                                              o["status"])
+    from paper_2504_00987_gb300 import _native as nat
+    import ctypes
+
+    res_s = (nat.Result * 4)()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert nat.load().labs_mts_run_static(ctypes.byref(P), 2, 0, 4, res_s, stream) == nat.LABS_OK
+    assert [(r.E, list(r.seq)[:2], r.steps) for r in res_s] == [(g["E"], g["seq"], g["steps"]) for g in a]
+
+
+def test_skew_reaches_exhaustive_skew_optimum(labs):
+    """N = 25: 304 replicas reach the skew-symmetric optimum of the
+    exhaustive enumeration (52), above the unrestricted optimum (36)."""
+    import tests.test_oracle_pins as pins
+
+    N = 25
+    E_skew = pins.skew_optimum(N)
+    P = labs.make_params(N, 50, target_E=E_skew, max_generations=2000, variant=SKEW)
+    res = labs.mts_run(P, 7, 0, 304)
+    assert all(r["E"] == E_skew and r["status"] == 1 for r in res)

@@ -451,6 +451,25 @@ def skew_optimum(N):
     return int(E.min())
 
 
+def test_bruteforce_skew_matches_enumeration(orc):
+    """The oracle's exhaustive skew optimum equals the numpy enumeration, and
+    its count of minimisers equals the count among all 2^N sequences
+    filtered by the skew condition (N = 13, 15, 17)."""
+    for N in (3, 5, 7, 9, 11, 13, 19, 21, 25):
+        assert orc.bruteforce_skew(N)[0] == skew_optimum(N)
+    for N in (13, 15, 17):
+        codes = np.arange(1 << N, dtype=np.int64)
+        S = np.where((codes[:, None] >> np.arange(N)) & 1, 1, -1)
+        n = (N + 1) // 2
+        keep = np.ones(len(codes), dtype=bool)
+        for i in range(1, n):
+            keep &= S[:, n + i - 1] == (-1) ** i * S[:, n - i - 1]
+        E = np.array([np_energy(x)[0] for x in S[keep]])
+        assert orc.bruteforce_skew(N) == (int(E.min()), int((E == E.min()).sum()))
+    with pytest.raises(ValueError):
+        orc.bruteforce_skew(20)
+
+
 def test_skew_optimum_by_filtering():
     """skew_optimum() equals the minimum over all 2^N sequences filtered by the
     skew condition, for N = 13..19."""
