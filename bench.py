@@ -283,9 +283,10 @@ def run_gpu(args) -> None:
                      "frac": achieved / peak, "traffic": traffic,
                      "note": "achieved = pair-terms (one scalar int32 accumulate each) per launch / "
                              "mean launch time; peak = 152 SMs x 128 int32 lanes x 2070 MHz"},
-        "e2e": {"value": flips_per_step_all / (e2e_step_ms / 1e3), "unit": "flip-evals/s",
-                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": REPLICAS * 64,
-                "call": "labs_mts_run (blocking; results copied to host)"},
+        "e2e": None if args.no_e2e else {
+            "value": flips_per_step_all / (e2e_step_ms / 1e3), "unit": "flip-evals/s",
+            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": REPLICAS * 64,
+            "call": "labs_mts_run (blocking; results copied to host)"},
         "gpu_launches": args.steps,
         "best_E": best_E, "best_merit_factor": N * N / (2.0 * best_E), "best_instance": best_inst,
         "wall_s_timed": wall,
