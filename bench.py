@@ -201,7 +201,9 @@ def run_gpu(args) -> None:
             pg.barrier()
         torch.cuda.synchronize()
 
-    global REPLICAS, STEPS_PER_REPLICA
+    global N, WORKLOAD, REPLICAS, STEPS_PER_REPLICA
+    if args.n:
+        N, WORKLOAD = args.n, f"replicas_n{args.n}"
     if args.replicas:
         REPLICAS = args.replicas
     if args.steps_per_replica:
@@ -269,7 +271,7 @@ def run_gpu(args) -> None:
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
         rec = json.load(open(TRAFFIC_FILE))
-        if rec.get("kernel_hash") == kernel_hash():
+        if rec.get("kernel_hash") == kernel_hash() and N == 64:  # captured on the N = 64 kernel
             traffic = rec.get("bytes_per_launch")
     line = {
         "metric": "flip-evals/s", "value": value, "unit": "flip-evals/s", "n_gpus": world,
@@ -448,11 +450,13 @@ def run_tts(args) -> None:
     """Time to a target E with every replica of the launch stopped by the global
     termination flag; p50/p99 over runs with distinct seeds, and an a * b^N fit of the
     median (Table III).  Targets (tests/golden/targets.json): the oracle's one-minute
-    best for N = 92..120, or the exact optimum (exhaustive search) for N = 16..32."""
+    best for N = 92..120, or the exact optimum (exhaustive search) for N = 16..36.
+    Each N also reports the median tabu steps of all replicas to the target (the
+    work, free of launch overhead), with the same fit."""
     torch, dev, pg, world, rank = gpu_context(args)
     import paper_2504_00987_gb300 as labs
 
-    kind = "optimum_n16_32" if args.tts_targets == "optimum" else "sweep_n92_120"
+    kind = "optimum_n16_36" if args.tts_targets == "optimum" else "sweep_n92_120"
     targets = load_targets(kind)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     reps = args.replicas or sms * 8
@@ -468,7 +472,10 @@ def run_tts(args) -> None:
             "unit": "s", "n_gpus": world, "higher_is_better": False, "dtype": "int32", "data": "synthetic",
             "config": {"workload": f"tts_{kind}: {reps} replicas with the global termination flag, K=100, "
                                    f"cap {cap} steps per replica", "runs_per_N": args.runs, "targets": kind},
-            "per_N": rows, "fit_median_a_b_pow_N": median_fit(rows)}), flush=True)
+            "per_N": rows, "fit_median_a_b_pow_N": median_fit(rows),
+            "fit_median_steps_a_b_pow_N": median_fit(rows, "p50_steps"),
+            f"fit_median_steps_a_b_pow_N_from_{args.fit_min_n}":
+                median_fit([r for r in rows if r["N"] >= args.fit_min_n], "p50_steps")}), flush=True)
 
 
 # Policies compared by the A/B time-to-target workload: the default reading of
@@ -492,7 +499,7 @@ def run_tts_ab(args) -> None:
 
     import paper_2504_00987_gb300 as labs
 
-    kind = "optimum_n16_32" if args.tts_targets == "optimum" else "sweep_n92_120"
+    kind = "optimum_n16_36" if args.tts_targets == "optimum" else "sweep_n92_120"
     targets = load_targets(kind)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     reps = args.replicas or sms * 8
@@ -544,7 +551,7 @@ def run_skew_ab(args) -> None:
     import paper_2504_00987_gb300 as labs
 
     skew_opt = load_targets("skew_optimum_odd_n17_45")
-    all_opt = load_targets("optimum_n16_32")
+    all_opt = load_targets("optimum_n16_36")
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     reps = args.replicas or sms * 8
     cap = args.steps_per_replica or 2_000_000
@@ -574,7 +581,7 @@ def run_skew_ab(args) -> None:
             "higher_is_better": False, "dtype": "int32", "data": "synthetic",
             "config": {"workload": f"skew_ab: odd N={Ns}, {reps} replicas with the global termination flag, "
                                    f"K=100, cap {cap} steps per replica", "runs_per_N": runs,
-                       "targets": "skew_optimum_odd_n17_45, optimum_n16_32"},
+                       "targets": "skew_optimum_odd_n17_45, optimum_n16_36"},
             "fit_unrestricted_p50_steps": median_fit(rows_u, "p50_steps"),
             "fit_restricted_p50_steps": median_fit(rows_s, "p50_steps"),
             "fit_unrestricted_p50_s": median_fit(rows_u), "fit_restricted_p50_s": median_fit(rows_s),
@@ -763,13 +770,16 @@ def main() -> None:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--replicas", type=int, default=0, help="profiling only: override replicas")
     ap.add_argument("--steps-per-replica", type=int, default=0, help="profiling only: override budget")
+    ap.add_argument("--n", type=int, default=0, help="profiling only: override N of the default workload")
     ap.add_argument("--workload", choices=["replicas_n64", "sweep_n92_120", "tts", "tts_ab", "skew_ab", "batch",
                                            "serve", "skew"],
                     default="replicas_n64")
     ap.add_argument("--runs", type=int, default=50, help="tts: runs per N")
     ap.add_argument("--tts-n", default="", help="tts: comma-separated N (default: all; tts_ab: first five)")
     ap.add_argument("--tts-targets", choices=["oracle", "optimum"], default="oracle",
-                    help="tts: oracle one-minute best (N=92..120) or exact optimum (N=16..32)")
+                    help="tts: oracle one-minute best (N=92..120) or exact optimum (N=16..36)")
+    ap.add_argument("--fit-min-n", type=int, default=30,
+                    help="tts: smallest N of the second steps fit (above the one-generation floor)")
     ap.add_argument("--requests", type=int, default=20_000, help="serve: requests")
     ap.add_argument("--baseline-requests", type=int, default=400, help="serve: plain-form prefix")
     ap.add_argument("--slots", type=int, default=0, help="serve: resident slots")

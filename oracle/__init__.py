@@ -140,6 +140,7 @@ def lib():
             ]
             L.orc_bruteforce.argtypes = [ctypes.c_int32, i32p, i64p, u64p]
             L.orc_bruteforce_skew.argtypes = [ctypes.c_int32, i32p, i64p]
+            L.orc_bruteforce_mt.argtypes = [ctypes.c_int32, ctypes.c_int32, i32p, i64p]
             L.orc_non_skew_pairs.argtypes = [u64p, ctypes.c_int32]
             L.orc_skew_deviation.argtypes = [u64p, ctypes.c_int32]
             L.orc_skew_deviation_mode.argtypes = [u64p, ctypes.c_int32, ctypes.c_int32]
@@ -304,6 +305,16 @@ def bruteforce(N: int):
         raise ValueError("bad arguments")
     return int(E[0]), int(n[0]), a.copy()
 
+
+
+def bruteforce_mt(N: int, threads: int):
+    """Exhaustive minimum over all 2^N sequences on `threads` threads (8 <= N <= 40):
+    (E_min, number of minimisers)."""
+    E = np.zeros(1, dtype=np.int32)
+    n = np.zeros(1, dtype=np.int64)
+    if lib().orc_bruteforce_mt(N, threads, _ptr(E, ctypes.c_int32), _ptr(n, ctypes.c_int64)) != 0:
+        raise ValueError("8 <= N <= 40 and threads >= 1")
+    return int(E[0]), int(n[0])
 
 
 def bruteforce_skew(N: int):

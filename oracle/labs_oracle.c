@@ -722,6 +722,82 @@ int32_t orc_bruteforce(int32_t N, int32_t* E_min, int64_t* n_min, uint64_t* argm
     return 0;
 }
 
+/* The same exhaustive search split over threads: the spins s[N-1-T..N-2]
+ * take each of their 2^T values in one chunk (T = 6), and every chunk runs
+ * the Gray-code walk above over s[0..N-2-T] from its own start, C_k from
+ * scratch.  s[N-1] = +1 as above (complements are equivalent). */
+typedef struct {
+    int32_t N, T, chunk0, chunks, step;
+    int64_t best, count;
+} bf_job;
+
+static void* bf_worker(void* arg) {
+    bf_job* J = (bf_job*)arg;
+    const int32_t N = J->N, low = N - 1 - J->T;
+    J->best = -1;
+    J->count = 0;
+    for (int ch = J->chunk0; ch < J->chunks; ch += J->step) {
+        int8_t s[64];
+        int32_t C[64];
+        for (int i = 0; i < N; ++i) s[i] = 1;
+        for (int b = 0; b < J->T; ++b)
+            if ((ch >> b) & 1) s[low + b] = -1;
+        int64_t E = energy_spins(s, N, C + 1);
+        int64_t best = E, count = 1;
+        const uint64_t total = (uint64_t)1 << low;
+        for (uint64_t step = 1; step < total; ++step) {
+            const int j = __builtin_ctzll(step);
+            for (int k = 1; k <= N - 1; ++k) {
+                int32_t d = 0;
+                if (j + k < N) d += s[j + k];
+                if (j - k >= 0) d += s[j - k];
+                C[k] += -2 * s[j] * d;
+            }
+            s[j] = (int8_t)-s[j];
+            E = 0;
+            for (int k = 1; k <= N - 1; ++k) E += (int64_t)C[k] * C[k];
+            if (E < best) {
+                best = E;
+                count = 1;
+            } else if (E == best) {
+                ++count;
+            }
+        }
+        if (J->best < 0 || best < J->best) {
+            J->best = best;
+            J->count = count;
+        } else if (best == J->best) {
+            J->count += count;
+        }
+    }
+    return 0;
+}
+
+int32_t orc_bruteforce_mt(int32_t N, int32_t threads, int32_t* E_min, int64_t* n_min) {
+    if (N < 8 || N > 40 || threads < 1 || !E_min) return -1;
+    const int T = 6, chunks = 1 << T;
+    if (threads > chunks) threads = chunks;
+    pthread_t th[64];
+    bf_job jobs[64];
+    for (int i = 0; i < threads; ++i) {
+        jobs[i] = (bf_job){N, T, i, chunks, threads, -1, 0};
+        pthread_create(&th[i], 0, bf_worker, &jobs[i]);
+    }
+    int64_t best = -1, count = 0;
+    for (int i = 0; i < threads; ++i) {
+        pthread_join(th[i], 0);
+        if (best < 0 || jobs[i].best < best) {
+            best = jobs[i].best;
+            count = jobs[i].count;
+        } else if (jobs[i].best == best) {
+            count += jobs[i].count;
+        }
+    }
+    *E_min = (int32_t)best;
+    if (n_min) *n_min = 2 * count;
+    return 0;
+}
+
 /* Exhaustive minimum of E over the skew-symmetric sequences of odd length N
  * (Sec. II.C): every assignment of the n = (N+1)/2 free spins, completed
  * by symmetrize() and scored from Eq. 2.  n_min counts the minimisers. */

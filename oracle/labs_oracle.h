@@ -140,6 +140,10 @@ int32_t orc_mts_run_many(const orc_params* P, uint64_t seed, uint32_t first_inst
  * the number of minimising sequences and the first one found. */
 int32_t orc_bruteforce(int32_t N, int32_t* E_min, int64_t* n_min, uint64_t* argmin);
 
+/* orc_bruteforce split over `threads` POSIX threads, for 8 <= N <= 40
+ * (no argmin); *n_min counts all minimisers (complements included). */
+int32_t orc_bruteforce_mt(int32_t N, int32_t threads, int32_t* E_min, int64_t* n_min);
+
 /* Exhaustive minimum of E over the 2^((N+1)/2) skew-symmetric sequences of
  * odd length N <= 45 (Sec. II.C); *n_min = number of minimisers. */
 int32_t orc_bruteforce_skew(int32_t N, int32_t* E_min, int64_t* n_min);

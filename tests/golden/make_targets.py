@@ -11,8 +11,9 @@ Two sets, each a fixed amount of oracle work so the file is reproducible
   serve_n32_160 -- for N = 32..160: the best E of one oracle replica (seed 0,
                    instance 0) with 4.3e5 * (64/N)^2 steps, about ten seconds
                    of one core ("the oracle's 10 s best").
-  optimum_n16_32 -- for N = 16..32: the exact minimum of E over all 2^N
-                   sequences (the oracle's exhaustive search).
+  optimum_n16_36 -- for N = 16..36: the exact minimum of E over all 2^N
+                   sequences and the number of minimisers (the oracle's
+                   exhaustive search, split over threads).
   skew_optimum_odd_n17_45 -- for odd N = 17..45: the exact minimum of E over
                    the 2^((N+1)/2) skew-symmetric sequences (Sec. II.C; the
                    oracle's exhaustive search over the free half).
@@ -74,11 +75,12 @@ def main() -> None:
             }
             print(f"serve: {len(Ns)} targets ({time.time() - t0:.0f}s)", flush=True)
         if args.only in (None, "optimum"):
-            Ns = list(range(16, 33))
-            opts = list(ex.map(oracle.bruteforce, Ns))
-            data["optimum_n16_32"] = {
-                "targets": {str(N): {"E": E, "minimisers": n} for N, (E, n, _) in zip(Ns, opts)}}
-            print(f"optimum: {len(Ns)} exhaustive minima ({time.time() - t0:.0f}s)", flush=True)
+            targets = {}
+            for N in range(16, 37):  # one N at a time, every thread on it
+                E, n = oracle.bruteforce_mt(N, args.threads)
+                targets[str(N)] = {"E": E, "minimisers": n}
+                print(f"optimum N={N}: E={E} ({time.time() - t0:.0f}s)", flush=True)
+            data["optimum_n16_36"] = {"targets": targets}
         if args.only in (None, "skew"):
             Ns = list(range(17, 46, 2))
             opts = list(ex.map(oracle.bruteforce_skew, Ns))

@@ -451,6 +451,15 @@ def skew_optimum(N):
     return int(E.min())
 
 
+def test_bruteforce_threads_match_single_thread(orc):
+    """The chunked exhaustive search gives the single-threaded walk's minimum
+    and number of minimisers, whatever the thread count."""
+    for N in (8, 13, 20, 24):
+        E, n, _ = orc.bruteforce(N)
+        for threads in (1, 3, 8):
+            assert orc.bruteforce_mt(N, threads) == (E, n)
+
+
 def test_bruteforce_skew_matches_enumeration(orc):
     """The oracle's exhaustive skew optimum equals the numpy enumeration, and
     its count of minimisers equals the count among all 2^N sequences
