@@ -100,10 +100,14 @@ struct PlaneMax {
 // trade popcounts (XU pipe) for logic (ALU pipe), which pays while the
 // step has registers to spare: for 7 or more words (six- and eight-word
 // sequences, N > 128) plain popcounts measured 14-21 % faster on GB300
-// and 2-16 % slower below.
+// and 2-16 % slower below.  Five words (four-word sequences) take one
+// full adder and two plain popcounts, about 1 % faster than two adders.
 template <int n, int weight>
 __device__ __forceinline__ int csa_popc(const uint32_t (&w)[n]) {
-    if constexpr (n <= 2 || (weight == 1 && n >= 7)) {
+    if constexpr (weight == 1 && n == 5) {
+        const uint32_t a = w[0], b = w[1], c = w[2];
+        return __popc(a ^ b ^ c) + 2 * __popc((a & b) | (c & (a | b))) + __popc(w[3]) + __popc(w[4]);
+    } else if constexpr (n <= 2 || (weight == 1 && n >= 7)) {
         int s = 0;
 #pragma unroll
         for (int i = 0; i < n; ++i) s += __popc(w[i]);

@@ -250,3 +250,26 @@ def test_replicas_n64_full_size_sampled(labs, orc):
     for i in sample:
         assert res[i]["E"] == ors[i]["E"] and res[i]["seq"] == [int(x) for x in ors[i]["seq"]]
         assert res[i]["generations"] == ors[i]["generations"]
+
+
+def test_sweep_n120_full_size_sampled(labs, orc):
+    """The sweep's largest launch: N=120 (two 64-bit words), K=100, one replica
+    per warp filling the GPU (8 per SM), 10^6 tabu steps each.  Three replicas
+    (first, middle, last) against the oracle, run on three host threads; every
+    replica used its budget and its energy matches its sequence."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    N, K, S = 120, 100, 1_000_000
+    R = torch.cuda.get_device_properties(0).multi_processor_count * 8
+    P = labs.make_params(N, K, max_steps=S)
+    res = labs.decode_results(labs.mts_launch(P, 0, 0, R), N)
+    assert all(r["steps"] == S for r in res)
+    seqs = np.array([r["seq"] for r in res], dtype=np.uint64)
+    E = labs.energy_batch(dev_seqs(seqs), N).cpu().numpy()
+    assert all(int(E[i]) == res[i]["E"] for i in range(R))
+    sample = [0, R // 2, R - 1]
+    with ThreadPoolExecutor(max_workers=len(sample)) as ex:
+        ors = list(ex.map(lambda i: orc.mts_run(orc.make_params(N, K, max_steps=S), 0, i)[0], sample))
+    for i, o in zip(sample, ors):
+        assert res[i]["E"] == o["E"] and res[i]["seq"] == [int(x) for x in o["seq"]]
+        assert res[i]["generations"] == o["generations"] and res[i]["steps"] == o["steps"]
