@@ -263,6 +263,19 @@ int32_t labs_skew_deviation_batch(const uint64_t* d_seqs, int32_t N, int64_t B, 
                                   labs_stream_t stream);
 
 /*
+ * labs_philox_batch -- the four words of Philox4x32-10 (Salmon et al., SC'11)
+ * under key (seed low 32 bits, seed high 32 bits) at each of B counters,
+ * i.e. the draws of the randomness contract above, computed by the device
+ * function every kernel draws with (for reproducing a decision, or for
+ * checking the generator).
+ *   d_ctr  device, B x 4 uint32 counters (instance, a, b, purpose), 16-byte aligned.
+ *   d_out  device, B x 4 uint32 words (x, y, z, w), 16-byte aligned.
+ * Asynchronous on `stream`.
+ */
+int32_t labs_philox_batch(uint64_t seed, const uint32_t* d_ctr, int64_t B, uint32_t* d_out,
+                          labs_stream_t stream);
+
+/*
  * Batched uneven instances: one persistent launch, captured once in a CUDA
  * graph, in which every warp takes the next instance from a device queue
  * and runs it to its stop condition.  Every instance must be bounded by a

@@ -114,6 +114,7 @@ def lib():
                 P(ctypes.c_uint32),
             )
             L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            L.orc_philox4x32_batch.argtypes = [u32p, ctypes.c_int64, ctypes.c_uint64, u32p]
             L.orc_philox4x64_10.argtypes = [u64p, u64p, u64p]
             L.orc_energy.argtypes = [u64p, ctypes.c_int32, i32p]
             L.orc_energy.restype = ctypes.c_int64
@@ -305,6 +306,14 @@ def bruteforce(N: int):
         raise ValueError("bad arguments")
     return int(E[0]), int(n[0]), a.copy()
 
+
+
+def philox4x32_batch(counters, seed: int):
+    """Philox4x32-10 words at each row of counters (B x 4 uint32) under key (seed lo, seed hi)."""
+    c = np.ascontiguousarray(counters, dtype=np.uint32)
+    out = np.zeros_like(c)
+    lib().orc_philox4x32_batch(_ptr(c, ctypes.c_uint32), c.shape[0], seed, _ptr(out, ctypes.c_uint32))
+    return out
 
 
 def bruteforce_mt(N: int, threads: int):

@@ -77,6 +77,11 @@ void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
     out[3] = x3;
 }
 
+void orc_philox4x32_batch(const uint32_t* ctr, int64_t B, uint64_t seed, uint32_t* out) {
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t i = 0; i < B; ++i) orc_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
+
 /* One draw of the RNG contract: word `which` of Philox4x32-10 at counter
  * (instance, a, b, purpose) under key (seed lo, seed hi). */
 static uint32_t draw(uint64_t seed, uint32_t instance, uint32_t a, uint32_t b, uint32_t purpose,

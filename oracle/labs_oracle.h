@@ -97,6 +97,9 @@ typedef struct orc_genlog {
 
 /* Philox4x32-10: out = bijection(ctr) under key. */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* orc_philox4x32_10 at B counters ctr[4i..4i+3] under key (seed lo, seed hi). */
+void orc_philox4x32_batch(const uint32_t* ctr, int64_t B, uint64_t seed, uint32_t* out);
 /* Philox4x64-10, same construction on 64-bit words (pinned against numpy). */
 void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
 

@@ -24,6 +24,7 @@ from .api import (  # noqa: F401
     mts_run,
     make_params,
     p_mut_u32,
+    philox_batch,
     skew_deviation_batch,
     tabu_run,
     version,

@@ -39,7 +39,7 @@ EXPORTED = [
     "labs_batch_device_results", "labs_batch_results", "labs_batch_get_mapping",
     "labs_batch_destroy", "labs_mts_batch_run", "labs_mts_run_static", "labs_serve_create",
     "labs_serve_submit", "labs_serve_poll", "labs_serve_cancel", "labs_serve_stats_get",
-    "labs_serve_destroy", "labs_skew_deviation_batch",
+    "labs_serve_destroy", "labs_skew_deviation_batch", "labs_philox_batch",
 ]
 STATIC_MAX_REPLICAS = 4096
 VARIANT_UNIFORM_CROSSOVER = 1
@@ -229,6 +229,8 @@ def load(path: str = LIB_PATH):
         L.labs_serve_destroy.argtypes = [vp]
         L.labs_skew_deviation_batch.restype = i32
         L.labs_skew_deviation_batch.argtypes = [vp, i32, i64, vp, vp]
+        L.labs_philox_batch.restype = i32
+        L.labs_philox_batch.argtypes = [u64, vp, i64, vp, vp]
         L.labs_mts_run_static.restype = i32
         L.labs_mts_run_static.argtypes = [ctypes.POINTER(Params), u64, u64, i64, RP, vp]
         _lib = L

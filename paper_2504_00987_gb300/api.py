@@ -62,6 +62,19 @@ def skew_deviation_batch(seqs: torch.Tensor, N: int, stream=None) -> torch.Tenso
     return out
 
 
+def philox_batch(counters: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
+    """Philox4x32-10 words of the randomness contract at B counters
+    (instance, a, b, purpose): an int32/uint32 CUDA tensor of shape (B, 4)."""
+    if not counters.is_cuda or counters.dtype not in (torch.int32, torch.uint32):
+        raise ValueError("counters must be an int32/uint32 CUDA tensor")
+    if counters.dim() != 2 or counters.shape[1] != 4:
+        raise ValueError("counters must have shape (B, 4)")
+    counters = counters.contiguous()
+    out = torch.empty_like(counters)
+    nat.check(nat.load().labs_philox_batch(seed, _ptr(counters), counters.shape[0], _ptr(out), _stream(stream)))
+    return out
+
+
 def tabu_run(start: torch.Tensor, N: int, seed: int, *, max_iter: int = -1, generation: int = 0,
              first_instance: int = 0, trace_cap: int = 0, variant: int = 0, stream=None) -> dict:
     """B independent tabu searches (Algorithm 2), one from each start sequence."""

@@ -255,6 +255,7 @@ int32_t labs_mts_run(const labs_params* P, uint64_t seed, uint64_t first_instanc
     LABS_TRY(make_mts_args(P, seed, first_instance, replicas, &a));
     if (replicas == 0) return ok();
     if (h_out == nullptr) return fail(LABS_EINVAL, "h_out is NULL");
+    NvtxRange range("labs mts run");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     labs_device_result* d_out = nullptr;
     uint32_t* d_glf = nullptr;

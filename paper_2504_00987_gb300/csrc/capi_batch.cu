@@ -177,6 +177,7 @@ extern "C" {
 int32_t labs_autotune(const labs_instance* h_inst, int64_t n, labs_stream_t stream, labs_mapping* out) {
     if (out == nullptr) return fail(LABS_EINVAL, "out is NULL");
     LABS_TRY(validate_instances(h_inst, n));
+    NvtxRange range("labs autotune");
     labs_mapping best{4, 1, LABS_ORDER_LPT, 0};
     if (n == 0) {
         *out = best;
@@ -303,6 +304,7 @@ int32_t labs_batch_create(const labs_instance* h_inst, int64_t n, const labs_map
 int32_t labs_batch_launch(labs_batch* b, labs_stream_t stream) {
     if (b == nullptr) return fail(LABS_EINVAL, "batch is NULL");
     if (b->n == 0) return ok();
+    NvtxRange range("labs batch launch");
     const cudaError_t e = cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     return ok();

@@ -190,6 +190,7 @@ void scheduler(labs_server* s) {
                 }
         }
         if (active.empty()) continue;
+        NvtxRange range("labs serve quantum");
         // upload new slots and the active list
         cudaError_t e = cudaSuccess;
         for (int32_t slot : fresh) {

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -26,6 +27,14 @@ int32_t check_variant(int32_t variant, int32_t N, bool skew_allowed, const char*
 // The given threshold, or floor(2^32 / spins mutated) if 0.
 uint32_t default_p_mut(int32_t N, uint32_t p_mut_u32, int32_t variant);
 int sm_count();
+// An NVTX range for the scope (host-side phases: quanta, batch launches,
+// autotuning, blocking runs); costs nothing unless a profiler is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 void fill_host_result(const labs_device_result& d, int32_t N, uint64_t instance, double seconds,
                       labs_result* o);
 

@@ -49,6 +49,16 @@ def test_philox4x64_matches_numpy(orc):
         assert list(raw) == list(a) + list(b)
 
 
+def test_philox_batch_equals_single_calls(orc):
+    """The batched oracle generator is the single-counter one at every row."""
+    rng = np.random.default_rng(3)
+    ctr = rng.integers(0, 1 << 32, size=(200, 4), dtype=np.uint64).astype(np.uint32)
+    seed = 0x0123456789ABCDEF
+    out = orc.philox4x32_batch(ctr, seed)
+    for r in range(200):
+        assert list(out[r]) == list(orc.philox4x32_10(list(ctr[r]), [seed & 0xFFFFFFFF, seed >> 32]))
+
+
 def test_philox4x32_statistics(orc):
     """Uniformity and independence of the 32-bit variant over a counter sweep."""
     outs = np.array([orc.philox4x32_10([i, 3, 0, 4], [5, 0]) for i in range(4096)], dtype=np.uint64)
