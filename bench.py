@@ -16,6 +16,7 @@ infrastructure) on the host cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -287,8 +288,10 @@ def run_gpu(args) -> None:
                              "mean launch time; peak = 152 SMs x 128 int32 lanes x 2070 MHz"},
         "e2e": None if args.no_e2e else {
             "value": flips_per_step_all / (e2e_step_ms / 1e3), "unit": "flip-evals/s",
-            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": REPLICAS * 64,
-            "call": "labs_mts_run (blocking; results copied to host)"},
+            "h2d_bytes_per_step": ctypes.sizeof(P), "d2h_bytes_per_step": REPLICAS * 64,
+            "call": "labs_mts_run (blocking; results copied to host)",
+            "inputs": "the instance definition (labs_params) goes with the launch; each replica's "
+                      "population is drawn on the device from (seed, instance), Algorithm 1"},
         "gpu_launches": args.steps,
         "best_E": best_E, "best_merit_factor": N * N / (2.0 * best_E), "best_instance": best_inst,
         "wall_s_timed": wall,
