@@ -135,15 +135,16 @@ class ClockSampler:
 # ---------------------------------------------------------------- CPU oracle
 
 
-def cpu_baseline_run(replicas: int, threads: int, steps: int) -> dict:
+def cpu_baseline_run(replicas: int, threads: int, steps: int, n: int | None = None) -> dict:
     import oracle
 
+    n = N if n is None else n
     oracle.build()
-    P = oracle.make_params(N, K, max_steps=steps)
+    P = oracle.make_params(n, K, max_steps=steps)
     t0 = time.perf_counter()
     res = oracle.mts_run_many(P, 0, 0, replicas, threads)
     dt = time.perf_counter() - t0
-    total = sum(r["steps"] for r in res) * N
+    total = sum(r["steps"] for r in res) * n
     return {"value": total / dt, "unit": "flip-evals/s", "cores": threads, "kind": "oracle",
             "sample": f"{replicas} of the {REPLICAS} replicas (instances 0..{replicas - 1}), "
                       f"{steps} tabu steps each, one replica per thread, {dt:.1f} s wall"}
@@ -377,8 +378,20 @@ def run_sweep(args) -> None:
                      "best_merit_factor": n * n / (2.0 * bE), "best_instance": bi})
         tot_flips += flips
         tot_ms += ms
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        # the oracle on the same N and parameters: one replica per host core, 10^4 steps each
+        cores = cpu_cores()
+        per_n = {}
+        for n in range(92, 121, 4):
+            per_n[str(n)] = cpu_baseline_run(cores, cores, 10_000, n)["value"]
+        cpu = {"value": statistics.mean(per_n.values()), "unit": "flip-evals/s", "cores": cores,
+               "kind": "oracle", "per_N": per_n,
+               "sample": f"per N: {cores} replicas (instances 0..{cores - 1}) x 10000 tabu steps, "
+                         f"one replica per thread; value = mean over N"}
     if rank == 0:
         print(json.dumps({
+            "cpu_baseline": cpu,
             "metric": "flip-evals/s", "value": tot_flips / (tot_ms / 1e3), "unit": "flip-evals/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "dtype": "int32", "data": "synthetic",
