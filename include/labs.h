@@ -90,6 +90,8 @@ typedef void* labs_stream_t; /* a cudaStream_t */
  *   (i, g, 2, 2) ...................... x replaced member
  *   (i, g, j/4, 3) .................... word j%4: mutation draw of bit j
  *   (i, g, t, 4) ...................... x tie pick, y tenure of tabu step t
+ *   (i, g, j/4, 5) .................... word j%4: uniform-crossover draw of bit j
+ *                                       (LABS_VARIANT_UNIFORM_CROSSOVER only)
  * randInt(a, b) = a + floor(u * (b - a + 1) / 2^32).
  * The generation step: with probability p_comb two binary tournaments
  * (lower E wins, lower index on ties) pick P1, P2 and the child is
