@@ -76,6 +76,7 @@ extern "C" {
 #define LABS_RUN_BUDGET 0  /* generation or step budget used up */
 #define LABS_RUN_REACHED 1 /* E(best) <= target_E */
 #define LABS_RUN_STOPPED 2 /* another replica of the same run reached target_E (GLF) */
+#define LABS_RUN_BADSTATE 3 /* labs_mts_resume: the state record belongs to another run */
 
 typedef void* labs_stream_t; /* a cudaStream_t */
 
@@ -249,6 +250,37 @@ int32_t labs_mts_launch(const labs_params* P, uint64_t seed, uint64_t first_inst
  */
 int32_t labs_mts_run(const labs_params* P, uint64_t seed, uint64_t first_instance,
                      int64_t replicas, labs_result* h_out, labs_stream_t stream);
+
+/*
+ * Checkpoint and resume.  Between two generations a replica's whole state
+ * is its population, their energies, its best sequence and its generation
+ * and step counters: every later draw is addressed by (instance,
+ * generation, index), so nothing else is needed to continue it exactly.
+ *
+ * labs_mts_state_bytes -- bytes of one replica's state record for (N, K):
+ *   an 80-byte header, then the population and its energies, padded to 16.
+ * labs_mts_resume -- labs_mts_launch with a state record per replica.
+ *   d_state  device, replicas * labs_mts_state_bytes(N, K) bytes, 16-byte
+ *            aligned, owned by the caller (copy it to the host to keep a
+ *            checkpoint, and back to continue).
+ *   resume   0: every replica starts from its initial population;
+ *            nonzero: every replica continues from its record, which must
+ *            have been written by this function for the same N, K, variant,
+ *            seed and instance (otherwise the record is left as it is and the
+ *            replica reports LABS_RUN_BADSTATE without running).
+ *   Budgets and the target are totals over the whole run (max_generations
+ *   counts from generation 0).  Each replica runs until P's stop condition,
+ *   then writes its result to d_out and its record to d_state.  A run
+ *   stopped by a generation budget and continued with a larger one equals
+ *   the run made straight to the larger budget, bit for bit; a step budget
+ *   may end a generation's tabu search early, and the continued run keeps
+ *   that shortened generation.  Traces are not recorded (P->d_trace must be
+ *   NULL); d_glf as in labs_mts_launch.  Asynchronous on `stream`.
+ */
+int64_t labs_mts_state_bytes(int32_t N, int32_t K);
+int32_t labs_mts_resume(const labs_params* P, uint64_t seed, uint64_t first_instance,
+                        int64_t replicas, void* d_state, int32_t resume, labs_device_result* d_out,
+                        uint32_t* d_glf, labs_stream_t stream);
 
 /*
  * labs_skew_deviation_batch -- deviation from skew-symmetry d(S) (Appendix A,

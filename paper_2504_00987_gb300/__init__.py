@@ -21,7 +21,9 @@ from .api import (  # noqa: F401
     decode_results,
     energy_batch,
     mts_launch,
+    mts_resume,
     mts_run,
+    mts_state_bytes,
     make_params,
     p_mut_u32,
     philox_batch,
@@ -35,6 +37,7 @@ from ._native import (  # noqa: F401
     REPLACE_WORST,
     RUN_BUDGET,
     RUN_REACHED,
+    RUN_BADSTATE,
     RUN_STOPPED,
     VARIANT_FIX_FIRST_SPIN,
     VARIANT_SKEW,

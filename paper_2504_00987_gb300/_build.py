@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "liblabs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cu", "capi_batch.cu", "energy.cu", "mts.cu", "mts_skew.cu", "batch.cu", "mts_static.cu", "serve.cu", "capi_serve.cu", "skew.cu", "philox.cu"]
+SOURCES = ["capi.cu", "capi_batch.cu", "energy.cu", "mts.cu", "mts_skew.cu", "mts_resume.cu", "batch.cu", "mts_static.cu", "serve.cu", "capi_serve.cu", "skew.cu", "philox.cu"]
 
 
 def nvcc_path() -> str:

@@ -31,6 +31,7 @@ REPLACE_WORST = 1
 RUN_BUDGET = 0
 RUN_REACHED = 1
 RUN_STOPPED = 2
+RUN_BADSTATE = 3
 
 # Every symbol include/labs.h declares.
 EXPORTED = [
@@ -40,6 +41,7 @@ EXPORTED = [
     "labs_batch_destroy", "labs_mts_batch_run", "labs_mts_run_static", "labs_serve_create",
     "labs_serve_submit", "labs_serve_poll", "labs_serve_cancel", "labs_serve_stats_get",
     "labs_serve_destroy", "labs_skew_deviation_batch", "labs_philox_batch",
+    "labs_mts_state_bytes", "labs_mts_resume",
 ]
 STATIC_MAX_REPLICAS = 4096
 VARIANT_UNIFORM_CROSSOVER = 1
@@ -229,6 +231,10 @@ def load(path: str = LIB_PATH):
         L.labs_serve_destroy.argtypes = [vp]
         L.labs_skew_deviation_batch.restype = i32
         L.labs_skew_deviation_batch.argtypes = [vp, i32, i64, vp, vp]
+        L.labs_mts_state_bytes.restype = i64
+        L.labs_mts_state_bytes.argtypes = [i32, i32]
+        L.labs_mts_resume.restype = i32
+        L.labs_mts_resume.argtypes = [ctypes.POINTER(Params), u64, u64, i64, vp, i32, vp, vp, vp]
         L.labs_philox_batch.restype = i32
         L.labs_philox_batch.argtypes = [u64, vp, i64, vp, vp]
         L.labs_mts_run_static.restype = i32

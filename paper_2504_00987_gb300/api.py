@@ -117,6 +117,33 @@ def mts_launch(params: nat.Params, seed: int, first_instance: int, replicas: int
     return out
 
 
+def mts_state_bytes(N: int, K: int) -> int:
+    """Bytes of one replica's resumable state record (labs_mts_state_bytes)."""
+    n = nat.load().labs_mts_state_bytes(N, K)
+    if n < 0:
+        raise nat.LabsError(nat.LABS_EINVAL, nat.load().labs_last_error().decode())
+    return int(n)
+
+
+def mts_resume(params: nat.Params, seed: int, first_instance: int, replicas: int, state: torch.Tensor,
+               resume: bool, out: torch.Tensor | None = None, glf_flag: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    """mts_launch with a resumable state record per replica in `state` (a CUDA
+    uint8 tensor of replicas * mts_state_bytes(N, K) bytes): start fresh
+    (resume=False) or continue every replica from its record (resume=True);
+    the records are rewritten at the end.  Returns the (replicas, 8) results."""
+    need = replicas * mts_state_bytes(params.N, params.K)
+    if not state.is_cuda or state.dtype != torch.uint8 or state.numel() < need or not state.is_contiguous():
+        raise ValueError(f"state must be a contiguous CUDA uint8 tensor of at least {need} bytes")
+    if out is None:
+        out = torch.empty((replicas, 8), dtype=torch.int64, device=state.device)
+    if params.glf and glf_flag is None:
+        glf_flag = torch.zeros(1, dtype=torch.int32, device=out.device)
+    nat.check(nat.load().labs_mts_resume(ctypes.byref(params), seed, first_instance, replicas, _ptr(state),
+                                         1 if resume else 0, _ptr(out), _ptr(glf_flag), _stream(stream)))
+    return out
+
+
 def decode_results(out: torch.Tensor, N: int, first_instance: int = 0) -> list[dict]:
     """labs_device_result rows (from mts_launch) -> dicts, on the host."""
     h = out.detach().cpu()

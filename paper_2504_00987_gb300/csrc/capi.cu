@@ -248,6 +248,35 @@ int32_t labs_mts_launch(const labs_params* P, uint64_t seed, uint64_t first_inst
     return ok();
 }
 
+int64_t labs_mts_state_bytes(int32_t N, int32_t K) {
+    if (N < 3 || N > LABS_MAX_N || K < 1 || K > LABS_MAX_K) {
+        fail(LABS_EINVAL, "N=%d or K=%d out of range", N, K);
+        return -1;
+    }
+    ok();
+    return static_cast<int64_t>(lgpu::resume_state_bytes(N, K));
+}
+
+int32_t labs_mts_resume(const labs_params* P, uint64_t seed, uint64_t first_instance, int64_t replicas,
+                        void* d_state, int32_t resume, labs_device_result* d_out, uint32_t* d_glf,
+                        labs_stream_t stream) {
+    lgpu::ResumeArgs ra;
+    LABS_TRY(make_mts_args(P, seed, first_instance, replicas, &ra.m));
+    if (P->d_trace != nullptr) return fail(LABS_EINVAL, "labs_mts_resume records no trace (d_trace must be NULL)");
+    if (replicas == 0) return ok();
+    LABS_TRY(check_dev(d_state, 16, "d_state", false));
+    LABS_TRY(check_dev(d_out, 16, "d_out", false));
+    LABS_TRY(check_dev(d_glf, 4, "d_glf", !P->glf));
+    ra.m.d_out = d_out;
+    ra.m.d_glf = P->glf ? d_glf : nullptr;
+    ra.d_state = static_cast<unsigned char*>(d_state);
+    ra.state_bytes = lgpu::resume_state_bytes(P->N, P->K);
+    ra.resume = resume != 0 ? 1 : 0;
+    const cudaError_t e = lgpu::launch_mts_resume(ra, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "mts resume kernel launch");
+    return ok();
+}
+
 int32_t labs_mts_run(const labs_params* P, uint64_t seed, uint64_t first_instance,
                      int64_t replicas, labs_result* h_out, labs_stream_t stream) {
     const auto t0 = std::chrono::steady_clock::now();

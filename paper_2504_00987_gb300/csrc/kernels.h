@@ -27,6 +27,32 @@ struct MtsArgs {
     size_t smem_per_warp;
 };
 
+// Resumable state of one replica (labs_mts_resume): this header, then K * NW
+// population words and K energies, the record padded to 16 bytes.  The run
+// it belongs to (N, K, variant, seed, instance) is stored and checked.
+struct ResumeHeader {
+    uint32_t best[2 * LABS_MAX_W];
+    int32_t E_best, status;
+    int64_t g, steps;
+    int32_t N, K, variant;
+    uint32_t instance;
+    uint64_t seed;
+};
+static_assert(sizeof(ResumeHeader) == 80, "resume header layout");
+
+inline size_t resume_state_bytes(int N, int K) {
+    const size_t nw = 2 * static_cast<size_t>((N + 63) / 64);
+    const size_t body = static_cast<size_t>(K) * nw * 4 + static_cast<size_t>(K) * 4;
+    return sizeof(ResumeHeader) + ((body + 15) & ~static_cast<size_t>(15));
+}
+
+struct ResumeArgs {
+    MtsArgs m;
+    unsigned char* d_state;  // replicas records of state_bytes each
+    size_t state_bytes;
+    int32_t resume;          // 0: start from the initial population
+};
+
 struct TabuArgs {
     const uint64_t* d_start;
     int32_t N;
@@ -84,6 +110,7 @@ cudaError_t launch_batch(const BatchArgs& a, int nwmax, int blocks, int warps_pe
 cudaError_t launch_mts(const MtsArgs& a, cudaStream_t stream);
 cudaError_t launch_tabu(const TabuArgs& a, cudaStream_t stream);
 cudaError_t launch_mts_skew(const MtsArgs& a, cudaStream_t stream);   // mts_skew.cu
+cudaError_t launch_mts_resume(const ResumeArgs& a, cudaStream_t stream);  // mts_resume.cu
 cudaError_t launch_tabu_skew(const TabuArgs& a, cudaStream_t stream);
 cudaError_t launch_energy(const uint64_t* d_seqs, int N, int64_t B, int32_t* d_E, int32_t* d_C,
                           cudaStream_t stream);

@@ -44,6 +44,97 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) mts_kernel(const MtsArgs 
     replica_run<NW, TRACE, SKEW>(cfg, pop, popE, Cs, trace, a.trace_cap, a.d_glf, a.d_out + r, lane);
 }
 
+// Memetic-Tabu with resumable state: each replica starts from its initial
+// population or from its record in ra.d_state, runs to its stop condition
+// and writes its record back (population, energies, best, counters).  The
+// draws are addressed by (instance, generation, index), so a run continued
+// from a record at a generation boundary equals the uninterrupted run.  A
+// record of another run (N, K, variant, seed or instance) is left untouched
+// and the replica reports LABS_RUN_BADSTATE.
+template <int NW, bool SKEW>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) mts_resume_kernel(const ResumeArgs ra) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const MtsArgs& a = ra.m;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + warp;
+    if (r >= a.replicas) return;
+
+    uint32_t* pop = reinterpret_cast<uint32_t*>(smem + static_cast<size_t>(warp) * a.smem_per_warp);
+    int32_t* popE = reinterpret_cast<int32_t*>(pop + a.K * NW);
+    int32_t* Cs = popE + a.K;
+    ReplicaCfg cfg;
+    cfg.N = a.N;
+    cfg.K = a.K;
+    cfg.p_comb_u32 = a.p_comb_u32;
+    cfg.p_mut_u32 = a.p_mut_u32;
+    cfg.replace_policy = a.replace_policy;
+    cfg.target_E = a.target_E;
+    cfg.max_generations = a.max_generations;
+    cfg.max_steps = a.max_steps;
+    cfg.max_iter = a.max_iter;
+    cfg.variant = a.variant;
+    cfg.inst = static_cast<uint32_t>(a.first_instance + static_cast<uint64_t>(r));
+    cfg.key = philox_key(a.seed);
+
+    unsigned char* rec = ra.d_state + static_cast<size_t>(r) * ra.state_bytes;
+    ResumeHeader* h = reinterpret_cast<ResumeHeader*>(rec);
+    uint32_t* hpop = reinterpret_cast<uint32_t*>(rec + sizeof(ResumeHeader));
+    int32_t* hpopE = reinterpret_cast<int32_t*>(hpop + a.K * NW);
+    ReplicaState<NW> st;
+    if (ra.resume) {
+        const bool match = h->N == a.N && h->K == a.K && h->variant == a.variant &&
+                           h->instance == cfg.inst && h->seed == a.seed;
+        if (!match) {
+            if (lane == 0) {
+                labs_device_result* o = a.d_out + r;
+                for (int w = 0; w < LABS_MAX_W; ++w) o->seq[w] = 0;
+                o->E = -1;
+                o->status = LABS_RUN_BADSTATE;
+                o->generations = 0;
+                o->steps = 0;
+                o->trace_len = 0;
+            }
+            return;
+        }
+        for (int x = lane; x < a.K * NW; x += 32) pop[x] = hpop[x];
+        for (int x = lane; x < a.K; x += 32) popE[x] = hpopE[x];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) st.best[w] = h->best[w];
+        st.E_best = h->E_best;
+        st.status = LABS_RUN_BUDGET;
+        st.g = h->g;
+        st.steps = h->steps;
+        __syncwarp();
+    } else {
+        replica_init<NW, SKEW>(cfg, pop, popE, st, lane);
+    }
+    int64_t trace_len = 0;
+    while (!replica_should_stop<NW>(cfg, st, a.d_glf))
+        replica_generation<NW, false, SKEW>(cfg, st, pop, popE, Cs, nullptr, 0, trace_len, a.d_glf, lane);
+    replica_store_result<NW>(st, 0, a.d_out + r, lane);
+    __syncwarp();
+    for (int x = lane; x < a.K * NW; x += 32) hpop[x] = pop[x];
+    for (int x = lane; x < a.K; x += 32) hpopE[x] = popE[x];
+    if (lane < 2 * LABS_MAX_W) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) v = (lane == w) ? st.best[w] : v;
+        h->best[lane] = v;
+    }
+    if (lane == 0) {
+        h->E_best = st.E_best;
+        h->status = st.status;
+        h->g = st.g;
+        h->steps = st.steps;
+        h->N = a.N;
+        h->K = a.K;
+        h->variant = a.variant;
+        h->instance = cfg.inst;
+        h->seed = a.seed;
+    }
+}
+
 template <int NW, bool TRACE, bool SKEW>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) tabu_kernel(const TabuArgs a) {
     __shared__ int32_t Cs_all[kWarpsPerBlock][32 * NW];
@@ -111,6 +202,27 @@ cudaError_t launch_mts_family(const MtsArgs& a, cudaStream_t stream) {
         case 2: return tr ? launch_mts_t<4, true, SKEW>(a, stream) : launch_mts_t<4, false, SKEW>(a, stream);
         case 3: return tr ? launch_mts_t<6, true, SKEW>(a, stream) : launch_mts_t<6, false, SKEW>(a, stream);
         default: return tr ? launch_mts_t<8, true, SKEW>(a, stream) : launch_mts_t<8, false, SKEW>(a, stream);
+    }
+}
+
+template <int NW, bool SKEW>
+cudaError_t launch_resume_w(const ResumeArgs& a, cudaStream_t stream) {
+    const size_t smem = a.m.smem_per_warp * kWarpsPerBlock;
+    cudaError_t e = cudaFuncSetAttribute(mts_resume_kernel<NW, SKEW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (a.m.replicas + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    mts_resume_kernel<NW, SKEW><<<static_cast<unsigned>(blocks), kWarpsPerBlock * 32, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool SKEW>
+cudaError_t launch_resume_family(const ResumeArgs& a, cudaStream_t stream) {
+    switch ((a.m.N + 63) / 64) {
+        case 1: return launch_resume_w<2, SKEW>(a, stream);
+        case 2: return launch_resume_w<4, SKEW>(a, stream);
+        case 3: return launch_resume_w<6, SKEW>(a, stream);
+        default: return launch_resume_w<8, SKEW>(a, stream);
     }
 }
 

@@ -100,6 +100,23 @@ def test_no_oracle_in_product():
                 assert "labs_oracle" not in text, f
 
 
+def test_resume_state_size_and_argument_errors_without_gpu(lib):
+    from paper_2504_00987_gb300 import _native as nat
+
+    # 80-byte header + K (NW + 1) 32-bit words, padded to 16 bytes
+    assert lib.labs_mts_state_bytes(64, 100) == 80 + 1200
+    assert lib.labs_mts_state_bytes(65, 7) == 80 + 144
+    assert lib.labs_mts_state_bytes(256, 3) == 80 + 112
+    assert lib.labs_mts_state_bytes(2, 10) == -1 and b"N=2" in lib.labs_last_error()
+    assert lib.labs_mts_state_bytes(64, 0) == -1
+    P = nat.Params(64, 100, 0, 0, 0, -1, 10, -1, -1, 0, None, 0, 0, 0)
+    assert lib.labs_mts_resume(ctypes.byref(P), 0, 0, 4, None, 0, None, None, None) == nat.LABS_EINVAL
+    assert b"d_state" in lib.labs_last_error()
+    P.trace_cap, P.d_trace = 4, 16  # any non-NULL trace is refused first
+    assert lib.labs_mts_resume(ctypes.byref(P), 0, 0, 4, None, 0, None, None, None) == nat.LABS_EINVAL
+    assert b"trace" in lib.labs_last_error()
+
+
 def test_batch_argument_errors_without_gpu(lib):
     from paper_2504_00987_gb300 import _native as nat
 
