@@ -6,7 +6,8 @@
 // and tabu list in registers.  Replicas never synchronise with each other;
 // the only cross-replica state is the optional global termination flag.
 // mts.cu instantiates the unrestricted kernels, mts_skew.cu the restricted
-// ones, so each translation unit compiles one family.
+// ones and mts_resume.cu the resumable ones (both kinds), so each
+// translation unit compiles one family.
 #pragma once
 
 #include <cuda_runtime.h>
