@@ -6,6 +6,7 @@ happens only when a source or header is newer than the library.
 """
 from __future__ import annotations
 
+import fcntl
 import glob
 import os
 import shutil
@@ -54,6 +55,19 @@ def up_to_date() -> bool:
 def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
     if not force and up_to_date():
         return LIB_PATH
+    # One build at a time (e.g. every rank of a multi-GPU job calls this at
+    # start-up): the others wait for the lock and then find the library fresh.
+    with open(os.path.join(HERE, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and up_to_date():
+                return LIB_PATH
+            return _build_locked(verbose, extra_flags)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose: bool, extra_flags: list[str] | None) -> str:
     os.makedirs(BUILD_DIR, exist_ok=True)
     nvcc = nvcc_path()
     flags = common_flags() + list(extra_flags or [])
