@@ -690,7 +690,9 @@ def run_serve(args) -> None:
             time.sleep(0.0002)
         return done, time.perf_counter() - t0
 
-    with labs.Server(max_slots=args.slots or 4096, max_N=160, max_K=100, quantum_steps=2000) as srv:
+    qsteps = args.quantum_steps if args.quantum_us == 0 else (1 << 40)
+    with labs.Server(max_slots=args.slots or 4096, max_N=160, max_K=100, quantum_steps=qsteps,
+                     quantum_us=args.quantum_us) as srv:
         done, wall = drive(lambda i: srv.submit(insts[i]), srv.poll)
         st = srv.stats()
     lat = np.array([done[k][1] for k in range(len(reqs))])
@@ -727,7 +729,9 @@ def run_serve(args) -> None:
             "higher_is_better": True, "dtype": "int32", "data": "synthetic",
             "config": {"workload": f"serve_poisson: {args.requests} requests at 200/s, N~U{{32..160}}, K=100, "
                                    "half target mode (oracle 10 s best, cap 1e7 steps), half 1e5 steps, seed 11",
-                       "slots": args.slots or 4096, "quantum_steps": 2000},
+                       "slots": args.slots or 4096,
+                       "quantum": (f"{args.quantum_us} us of device time per slot" if args.quantum_us
+                                   else f"{args.quantum_steps} tabu steps per slot")},
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "p50_target_mode": float(np.percentile(lat[tmode], 50)) if tmode.any() else None,
                           "p99_target_mode": float(np.percentile(lat[tmode], 99)) if tmode.any() else None,
@@ -799,6 +803,9 @@ def main() -> None:
     ap.add_argument("--requests", type=int, default=20_000, help="serve: requests")
     ap.add_argument("--baseline-requests", type=int, default=400, help="serve: plain-form prefix")
     ap.add_argument("--slots", type=int, default=0, help="serve: resident slots")
+    ap.add_argument("--quantum-steps", type=int, default=2000, help="serve: tabu steps per slot per quantum")
+    ap.add_argument("--quantum-us", type=int, default=4000,
+                    help="serve: device-time budget per slot per quantum (0: the step count instead)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

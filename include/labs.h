@@ -371,6 +371,10 @@ typedef struct labs_serve_opts {
     int64_t hbm_budget_bytes;   /* cap on the populations resident at once; 0: no cap */
     int64_t quantum_timeout_ms; /* longest wait for one quantum before the server fails with
                                    LABS_ETIMEOUT; 0: 60000 */
+    int64_t quantum_us;         /* > 0: a slot also suspends at the first generation boundary
+                                   after this many microseconds of the quantum (device clock;
+                                   at least one generation per quantum), so slots of every N
+                                   share a quantum evenly; 0: steps only */
 } labs_serve_opts;
 
 /* One solve request: an MTS instance; max_steps or max_generations must bound it. */

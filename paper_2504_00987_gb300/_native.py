@@ -151,6 +151,7 @@ class ServeOpts(ctypes.Structure):
         ("queue_capacity", ctypes.c_int64),
         ("hbm_budget_bytes", ctypes.c_int64),
         ("quantum_timeout_ms", ctypes.c_int64),
+        ("quantum_us", ctypes.c_int64),
     ]
 
 

@@ -298,9 +298,9 @@ class Server:
     def __init__(self, max_slots: int = 1024, max_N: int = 256, max_K: int = 128,
                  warps_per_block: int = 4, quantum_steps: int = 2000,
                  queue_capacity: int = 1 << 20, hbm_budget_bytes: int = 0,
-                 quantum_timeout_ms: int = 0):
+                 quantum_timeout_ms: int = 0, quantum_us: int = 0):
         opts = nat.ServeOpts(max_slots, max_N, max_K, warps_per_block, quantum_steps,
-                             queue_capacity, hbm_budget_bytes, quantum_timeout_ms)
+                             queue_capacity, hbm_budget_bytes, quantum_timeout_ms, quantum_us)
         L = nat.load()
         self._h = L.labs_serve_create(ctypes.byref(opts))
         if not self._h:

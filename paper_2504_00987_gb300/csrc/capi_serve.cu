@@ -215,6 +215,7 @@ void scheduler(labs_server* s) {
         a.active = s->d_active;
         a.n_active = n;
         a.quantum_steps = s->opts.quantum_steps;
+        a.quantum_ns = static_cast<uint64_t>(s->opts.quantum_us) * 1000u;
         a.out = s->d_out;
         a.done = s->d_done;
         a.quantum_used = s->d_used;
@@ -294,8 +295,8 @@ labs_server* labs_serve_create(const labs_serve_opts* o) {
         return nullptr;
     }
     if (o->quantum_steps < 1 || o->queue_capacity < 0 || o->hbm_budget_bytes < 0 ||
-        o->quantum_timeout_ms < 0) {
-        fail(LABS_EINVAL, "quantum_steps >= 1, queue_capacity/hbm_budget/timeout >= 0");
+        o->quantum_timeout_ms < 0 || o->quantum_us < 0 || o->quantum_us > (int64_t{1} << 40)) {
+        fail(LABS_EINVAL, "quantum_steps >= 1, queue_capacity/hbm_budget/timeout/quantum_us >= 0");
         return nullptr;
     }
     labs_server* s = new (std::nothrow) labs_server();

@@ -95,6 +95,7 @@ struct ServeArgs {
     const int32_t* active;       // slot of each active index
     int32_t n_active;
     int64_t quantum_steps;       // a slot stops at the first generation boundary past this
+    uint64_t quantum_ns;         // > 0: ... or past this much device time (%globaltimer)
     labs_device_result* out;     // per active index (finished slots only)
     int32_t* done;               // per active index
     int64_t* quantum_used;       // steps each active slot took in this quantum

@@ -7,7 +7,9 @@
 // generation boundary, where the replica's state is exactly (population,
 // best, g, steps), so a request's trajectory does not depend on the quantum
 // size or on which other requests share the launch.  The kernel never waits
-// on anything: it is bounded by the quantum and one generation.
+// on anything: it is bounded by the quantum and one generation.  The quantum
+// is a step count, and optionally a device-time budget, so that slots of
+// small N are not held to the pace of the largest one.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -30,6 +32,14 @@ __device__ __forceinline__ ReplicaCfg serve_cfg(const labs_instance& in) {
     c.inst = static_cast<uint32_t>(in.instance);
     c.key = philox_key(in.seed);
     return c;
+}
+
+// Device time in nanoseconds (the %globaltimer register), read by lane 0 and
+// broadcast so that every lane takes the same decision.
+__device__ __forceinline__ uint64_t warp_globaltimer(int lane) {
+    uint64_t t = 0;
+    if (lane == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return __shfl_sync(kFull, t, 0);
 }
 
 template <int NW>
@@ -60,12 +70,14 @@ __device__ void serve_slot(const ServeArgs& a, int i, int slot, const labs_insta
     }
     int64_t used = 0, trace_len = 0;
     bool finished = false;
-    for (;;) {
+    const uint64_t t0 = a.quantum_ns ? warp_globaltimer(lane) : 0;
+    for (int gens = 0;; ++gens) {
         if (replica_should_stop<NW>(cfg, st, nullptr)) {
             finished = true;
             break;
         }
         if (used >= a.quantum_steps) break;
+        if (a.quantum_ns && gens > 0 && warp_globaltimer(lane) - t0 >= a.quantum_ns) break;
         used += replica_generation<NW>(cfg, st, pop, popE, Cs, nullptr, 0, trace_len, nullptr, lane);
     }
     if (finished) {

@@ -143,10 +143,14 @@ def test_batch_argument_errors_without_gpu(lib):
 def test_serve_argument_errors_without_gpu(lib):
     from paper_2504_00987_gb300 import _native as nat
 
-    bad = nat.ServeOpts(0, 64, 100, 4, 1000, 10, 0, 0)
+    bad = nat.ServeOpts(0, 64, 100, 4, 1000, 10, 0, 0, 0)
     assert not lib.labs_serve_create(ctypes.byref(bad))
     assert b"max_slots" in lib.labs_last_error()
-    bad = nat.ServeOpts(16, 64, 100, 3, 1000, 10, 0, 0)
+    bad = nat.ServeOpts(16, 64, 100, 3, 1000, 10, 0, 0, 0)
     assert not lib.labs_serve_create(ctypes.byref(bad))
+    bad = nat.ServeOpts(16, 64, 100, 4, 1000, 10, 0, 0, -5)  # negative time budget
+    assert not lib.labs_serve_create(ctypes.byref(bad))
+    assert b"quantum_us" in lib.labs_last_error()
+    assert ctypes.sizeof(nat.ServeOpts) == 4 * 4 + 8 * 5
     assert lib.labs_serve_destroy(None) == nat.LABS_OK
     assert lib.labs_serve_poll(None, 1, None) == nat.LABS_EINVAL

@@ -90,6 +90,21 @@ def test_quantum_size_and_budget_do_not_change_results(labs):
         assert same(a, b) and same(a, c)
 
 
+def test_time_budget_quanta_do_not_change_results(labs):
+    """Quanta ended by a device-time budget (slots of every N suspend at the
+    first generation boundary past it) give the results of step quanta."""
+    reqs = random_requests(labs, 40, seed=33, steps=(1000, 30_000))
+    outs = []
+    for kw in (dict(quantum_steps=500), dict(quantum_steps=1 << 40, quantum_us=300),
+               dict(quantum_steps=1 << 40, quantum_us=3000)):
+        with labs.Server(max_slots=12, max_N=160, max_K=100, **kw) as srv:
+            outs.append(wait_all(srv, [srv.submit(r) for r in reqs]))
+            st = srv.stats()
+        assert st["completed"] == 40 and st["failed"] == 0
+    for a, b, c in zip(*outs):
+        assert same(a, b) and same(a, c)
+
+
 def test_target_requests_stop_on_target(labs):
     reqs = [labs.make_instance(40, 50, seed=3, instance=i, target_E=140, max_steps=2_000_000)
             for i in range(12)]
