@@ -349,12 +349,13 @@ def timed_launch(torch, fn, stream):
 
 
 def run_sweep(args) -> None:
-    """N = 92, 96, ..., 120 (two words), one K=100 population per warp, 8 warps per SM."""
+    """N = 92, 96, ..., 120 (two words), one K=100 population per warp, 16 warps per SM
+    (4 % more flip-evals/s than 8 on GB300: more warps hide the step's latencies)."""
     torch, dev, pg, world, rank = gpu_context(args)
     import paper_2504_00987_gb300 as labs
 
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    reps = args.replicas or sms * 8
+    reps = args.replicas or sms * 16
     steps = args.steps_per_replica or 1_000_000
     first, _ = parallel.shard(world, rank, reps)
     stream = torch.cuda.current_stream()

@@ -254,13 +254,13 @@ def test_replicas_n64_full_size_sampled(labs, orc):
 
 def test_sweep_n120_full_size_sampled(labs, orc):
     """The sweep's largest launch: N=120 (two 64-bit words), K=100, one replica
-    per warp filling the GPU (8 per SM), 10^6 tabu steps each.  Three replicas
+    per warp filling the GPU (16 per SM), 10^6 tabu steps each.  Three replicas
     (first, middle, last) against the oracle, run on three host threads; every
     replica used its budget and its energy matches its sequence."""
     from concurrent.futures import ThreadPoolExecutor
 
     N, K, S = 120, 100, 1_000_000
-    R = torch.cuda.get_device_properties(0).multi_processor_count * 8
+    R = torch.cuda.get_device_properties(0).multi_processor_count * 16
     P = labs.make_params(N, K, max_steps=S)
     res = labs.decode_results(labs.mts_launch(P, 0, 0, R), N)
     assert all(r["steps"] == S for r in res)
