@@ -1,6 +1,7 @@
 // labs_device.cuh -- device primitives of the LABS solver (sm_103a).
 //
-// Sequences live in registers as NW = 2W 32-bit words, bit i of the vector
+// Sequences live in registers as NW 32-bit words (2W for W 64-bit words, or
+// 3 for 64 < N <= 96), bit i of the vector
 // (word i / 32, bit i % 32) holding spin s_{i+1} (1 <-> +1).  A warp owns one
 // sequence; every lane keeps an identical copy of the words ("warp-uniform")
 // and lane l owns the indices l + 32q, q = 0 .. NW-1, of the per-index

@@ -146,8 +146,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) tabu_kernel(const TabuArg
     const int N = a.N;
     const uint2 key = philox_key(a.seed);
     const uint32_t inst = static_cast<uint32_t>(a.first_instance + static_cast<uint64_t>(b));
+    constexpr int ROW = (NW + 1) & ~1;  // 32-bit words per row: whole 64-bit words
     uint32_t seq[NW];
-    load_seq<NW>(reinterpret_cast<const uint32_t*>(a.d_start) + b * NW, seq);
+    load_seq<NW>(reinterpret_cast<const uint32_t*>(a.d_start) + b * ROW, seq);
 #pragma unroll
     for (int w = 0; w < NW; ++w) seq[w] &= word_lowmask(w, N);  // bits >= N are ignored
     if constexpr (SKEW) skew_complete<NW>(seq, N);              // the free half decides
@@ -172,11 +173,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) tabu_kernel(const TabuArg
                  : tabu_search<NW, TRACE, false>(seq, N, key, inst, a.generation, max_iter, -1,
                                                  Cs_all[warp], trace, a.trace_cap, trace_len, lane);
     }
-    if (lane < NW) {
+    if (lane < ROW) {
         uint32_t v = 0;
 #pragma unroll
         for (int w = 0; w < NW; ++w) v = (lane == w) ? seq[w] : v;
-        reinterpret_cast<uint32_t*>(a.d_best)[b * NW + lane] = v;
+        reinterpret_cast<uint32_t*>(a.d_best)[b * ROW + lane] = v;
     }
     if (lane == 0) {
         a.d_bestE[b] = to.E_best;
@@ -195,13 +196,18 @@ cudaError_t launch_mts_t(const MtsArgs& a, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
+// 32-bit words per sequence in registers: whole 64-bit words, except three
+// for 64 < N <= 96 (a quarter less work per step than four).
+inline int word_count(int N) { return N <= 64 ? 2 : N <= 96 ? 3 : N <= 128 ? 4 : N <= 192 ? 6 : 8; }
+
 template <bool SKEW>
 cudaError_t launch_mts_family(const MtsArgs& a, cudaStream_t stream) {
     const bool tr = a.d_trace != nullptr;
-    switch ((a.N + 63) / 64) {
-        case 1: return tr ? launch_mts_t<2, true, SKEW>(a, stream) : launch_mts_t<2, false, SKEW>(a, stream);
-        case 2: return tr ? launch_mts_t<4, true, SKEW>(a, stream) : launch_mts_t<4, false, SKEW>(a, stream);
-        case 3: return tr ? launch_mts_t<6, true, SKEW>(a, stream) : launch_mts_t<6, false, SKEW>(a, stream);
+    switch (word_count(a.N)) {
+        case 2: return tr ? launch_mts_t<2, true, SKEW>(a, stream) : launch_mts_t<2, false, SKEW>(a, stream);
+        case 3: return tr ? launch_mts_t<3, true, SKEW>(a, stream) : launch_mts_t<3, false, SKEW>(a, stream);
+        case 4: return tr ? launch_mts_t<4, true, SKEW>(a, stream) : launch_mts_t<4, false, SKEW>(a, stream);
+        case 6: return tr ? launch_mts_t<6, true, SKEW>(a, stream) : launch_mts_t<6, false, SKEW>(a, stream);
         default: return tr ? launch_mts_t<8, true, SKEW>(a, stream) : launch_mts_t<8, false, SKEW>(a, stream);
     }
 }
@@ -219,10 +225,11 @@ cudaError_t launch_resume_w(const ResumeArgs& a, cudaStream_t stream) {
 
 template <bool SKEW>
 cudaError_t launch_resume_family(const ResumeArgs& a, cudaStream_t stream) {
-    switch ((a.m.N + 63) / 64) {
-        case 1: return launch_resume_w<2, SKEW>(a, stream);
-        case 2: return launch_resume_w<4, SKEW>(a, stream);
-        case 3: return launch_resume_w<6, SKEW>(a, stream);
+    switch (word_count(a.m.N)) {
+        case 2: return launch_resume_w<2, SKEW>(a, stream);
+        case 3: return launch_resume_w<3, SKEW>(a, stream);
+        case 4: return launch_resume_w<4, SKEW>(a, stream);
+        case 6: return launch_resume_w<6, SKEW>(a, stream);
         default: return launch_resume_w<8, SKEW>(a, stream);
     }
 }
@@ -239,10 +246,11 @@ cudaError_t launch_tabu_w(const TabuArgs& a, cudaStream_t stream) {
 
 template <bool SKEW>
 cudaError_t launch_tabu_family(const TabuArgs& a, cudaStream_t stream) {
-    switch ((a.N + 63) / 64) {
-        case 1: return launch_tabu_w<2, SKEW>(a, stream);
-        case 2: return launch_tabu_w<4, SKEW>(a, stream);
-        case 3: return launch_tabu_w<6, SKEW>(a, stream);
+    switch (word_count(a.N)) {
+        case 2: return launch_tabu_w<2, SKEW>(a, stream);
+        case 3: return launch_tabu_w<3, SKEW>(a, stream);
+        case 4: return launch_tabu_w<4, SKEW>(a, stream);
+        case 6: return launch_tabu_w<6, SKEW>(a, stream);
         default: return launch_tabu_w<8, SKEW>(a, stream);
     }
 }

@@ -94,11 +94,21 @@ template <int NW, bool SKEW = false>
 __device__ void replica_init(const ReplicaCfg& a, uint32_t* __restrict__ pop,
                              int32_t* __restrict__ popE, ReplicaState<NW>& st, int lane) {
     const int N = a.N, K = a.K;
-    for (int idx = lane; idx < K * (NW / 2); idx += 32) {
-        const int p = idx / (NW / 2), w64 = idx % (NW / 2);
-        const uint4 d = draw4(a.key, a.inst, static_cast<uint32_t>(p), static_cast<uint32_t>(w64), kPurposeInit);
-        pop[p * NW + 2 * w64] = d.x & word_lowmask(2 * w64, N);
-        pop[p * NW + 2 * w64 + 1] = d.y & word_lowmask(2 * w64 + 1, N);
+    if constexpr (NW & 1) {  // the last 64-bit word keeps only its low half
+        constexpr int W64 = (NW + 1) / 2;
+        for (int idx = lane; idx < K * W64; idx += 32) {
+            const int p = idx / W64, w64 = idx % W64;
+            const uint4 d = draw4(a.key, a.inst, static_cast<uint32_t>(p), static_cast<uint32_t>(w64), kPurposeInit);
+            pop[p * NW + 2 * w64] = d.x & word_lowmask(2 * w64, N);
+            if (2 * w64 + 1 < NW) pop[p * NW + 2 * w64 + 1] = d.y & word_lowmask(2 * w64 + 1, N);
+        }
+    } else {
+        for (int idx = lane; idx < K * (NW / 2); idx += 32) {
+            const int p = idx / (NW / 2), w64 = idx % (NW / 2);
+            const uint4 d = draw4(a.key, a.inst, static_cast<uint32_t>(p), static_cast<uint32_t>(w64), kPurposeInit);
+            pop[p * NW + 2 * w64] = d.x & word_lowmask(2 * w64, N);
+            pop[p * NW + 2 * w64 + 1] = d.y & word_lowmask(2 * w64 + 1, N);
+        }
     }
     __syncwarp();
     if constexpr (SKEW) {

@@ -116,8 +116,13 @@ __global__ void __launch_bounds__(256) serve_quantum_kernel(const ServeArgs a) {
     const int W = (in.N + 63) / 64;
     if (W == 1) {
         serve_slot<2>(a, i, slot, in, base, lane);
-    } else if (W == 2) {
-        if constexpr (NWMAX >= 4) serve_slot<4>(a, i, slot, in, base, lane);
+    } else if (W == 2) {  // three 32-bit words up to N = 96
+        if constexpr (NWMAX >= 4) {
+            if (in.N <= 96)
+                serve_slot<3>(a, i, slot, in, base, lane);
+            else
+                serve_slot<4>(a, i, slot, in, base, lane);
+        }
     } else if (W == 3) {
         if constexpr (NWMAX >= 6) serve_slot<6>(a, i, slot, in, base, lane);
     } else {

@@ -90,7 +90,7 @@ struct TabuOut {
 // bitlen(32*NW - 1) + 1 two's-complement bits.
 template <int NW>
 struct PlaneMax {
-    static constexpr int value = (NW == 2) ? 7 : (NW == 4) ? 8 : 9;
+    static constexpr int value = (NW == 2) ? 7 : (NW <= 4) ? 8 : 9;
 };
 
 // sum_i popc(w[i]) * weight for n words, carry-save compressed: full
@@ -162,9 +162,10 @@ __device__ __forceinline__ void score_planes(const int32_t (&c)[NW], const uint3
 // are updated incrementally per move.
 template <int NW>
 __device__ __forceinline__ void prefix_own(const int32_t (&c)[NW], int lane, int32_t (&pc)[NW]) {
+    constexpr int NP = NW & ~1;  // chunks scanned in pairs
     int32_t carry = 0;
 #pragma unroll
-    for (int q = 0; q < NW; q += 2) {
+    for (int q = 0; q < NP; q += 2) {
         int32_t v = c[q] + c[q + 1] * 65536;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -179,6 +180,15 @@ __device__ __forceinline__ void prefix_own(const int32_t (&c)[NW], int lane, int
         pc[q] = carry + lo;
         pc[q + 1] = carry + lo31 + hi;
         carry += lo31 + hi31;
+    }
+    if constexpr (NW & 1) {  // an odd word count leaves one chunk, scanned alone
+        int32_t v = c[NW - 1];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t n = __shfl_up_sync(kFull, v, o);
+            if (lane >= o) v += n;
+        }
+        pc[NW - 1] = carry + v;
     }
 }
 

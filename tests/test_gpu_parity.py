@@ -142,7 +142,8 @@ def check_against_oracle(orc, res, trace, N, K, seed, first, cap, **kw):
             assert np.array_equal(trace[r, : len(otr)], otr)
 
 
-@pytest.mark.parametrize("N,K", [(3, 2), (8, 5), (24, 100), (40, 33), (64, 100), (65, 7), (100, 50),
+@pytest.mark.parametrize("N,K", [(3, 2), (8, 5), (24, 100), (40, 33), (64, 100), (65, 7), (80, 40), (96, 64),
+                                 (97, 9), (100, 50),
                                  (128, 100), (129, 20), (200, 10), (256, 3)])
 @pytest.mark.parametrize("policy", [0, 1])
 def test_mts_trajectories(labs, orc, N, K, policy):
