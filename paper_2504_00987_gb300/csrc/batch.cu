@@ -5,8 +5,7 @@
 // longest first by the host), runs it to its stop condition with the
 // replica engine and writes its result at the instance's original index.
 // Instances of different word counts share the launch: the warp dispatches
-// on the instance's word count (three 32-bit words up to N = 96, else
-// whole 64-bit words).  Per-instance results do not depend on
+// on W = ceil(N/64) per instance.  Per-instance results do not depend on
 // the mapping or on the other instances (every draw is keyed by the
 // instance's own seed and instance number).
 #include <cuda_runtime.h>
@@ -59,13 +58,11 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs a) {
         const int W = (in.N + 63) / 64;
         if (W == 1) {
             run_instance<2>(cfg, base, out, lane);
-        } else if (W == 2) {  // three 32-bit words up to N = 96
-            if constexpr (NWMAX >= 4) {
-                if (in.N <= 96)
-                    run_instance<3>(cfg, base, out, lane);
-                else
-                    run_instance<4>(cfg, base, out, lane);
-            }
+        } else if (W == 2) {
+            // four words up to N = 128: a three-word path in this kernel cost the
+            // four-word one its registers (172 -> 128) and the batch's makespan,
+            // which the longest (largest-N) instances set, 12 % on GB300
+            if constexpr (NWMAX >= 4) run_instance<4>(cfg, base, out, lane);
         } else if (W == 3) {
             if constexpr (NWMAX >= 6) run_instance<6>(cfg, base, out, lane);
         } else {
