@@ -197,8 +197,11 @@ cudaError_t launch_mts_t(const MtsArgs& a, cudaStream_t stream) {
 }
 
 // 32-bit words per sequence in registers: whole 64-bit words, except three
-// for 64 < N <= 96 (a quarter less work per step than four).
-inline int word_count(int N) { return N <= 64 ? 2 : N <= 96 ? 3 : N <= 128 ? 4 : N <= 192 ? 6 : 8; }
+// for 64 < N <= 96 and five for 128 < N <= 160 (less work per step than the
+// next whole 64-bit word count).
+inline int word_count(int N) {
+    return N <= 64 ? 2 : N <= 96 ? 3 : N <= 128 ? 4 : N <= 160 ? 5 : N <= 192 ? 6 : 8;
+}
 
 template <bool SKEW>
 cudaError_t launch_mts_family(const MtsArgs& a, cudaStream_t stream) {
@@ -207,6 +210,7 @@ cudaError_t launch_mts_family(const MtsArgs& a, cudaStream_t stream) {
         case 2: return tr ? launch_mts_t<2, true, SKEW>(a, stream) : launch_mts_t<2, false, SKEW>(a, stream);
         case 3: return tr ? launch_mts_t<3, true, SKEW>(a, stream) : launch_mts_t<3, false, SKEW>(a, stream);
         case 4: return tr ? launch_mts_t<4, true, SKEW>(a, stream) : launch_mts_t<4, false, SKEW>(a, stream);
+        case 5: return tr ? launch_mts_t<5, true, SKEW>(a, stream) : launch_mts_t<5, false, SKEW>(a, stream);
         case 6: return tr ? launch_mts_t<6, true, SKEW>(a, stream) : launch_mts_t<6, false, SKEW>(a, stream);
         default: return tr ? launch_mts_t<8, true, SKEW>(a, stream) : launch_mts_t<8, false, SKEW>(a, stream);
     }
@@ -229,6 +233,7 @@ cudaError_t launch_resume_family(const ResumeArgs& a, cudaStream_t stream) {
         case 2: return launch_resume_w<2, SKEW>(a, stream);
         case 3: return launch_resume_w<3, SKEW>(a, stream);
         case 4: return launch_resume_w<4, SKEW>(a, stream);
+        case 5: return launch_resume_w<5, SKEW>(a, stream);
         case 6: return launch_resume_w<6, SKEW>(a, stream);
         default: return launch_resume_w<8, SKEW>(a, stream);
     }
@@ -250,6 +255,7 @@ cudaError_t launch_tabu_family(const TabuArgs& a, cudaStream_t stream) {
         case 2: return launch_tabu_w<2, SKEW>(a, stream);
         case 3: return launch_tabu_w<3, SKEW>(a, stream);
         case 4: return launch_tabu_w<4, SKEW>(a, stream);
+        case 5: return launch_tabu_w<5, SKEW>(a, stream);
         case 6: return launch_tabu_w<6, SKEW>(a, stream);
         default: return launch_tabu_w<8, SKEW>(a, stream);
     }

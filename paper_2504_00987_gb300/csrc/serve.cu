@@ -123,8 +123,13 @@ __global__ void __launch_bounds__(256) serve_quantum_kernel(const ServeArgs a) {
             else
                 serve_slot<4>(a, i, slot, in, base, lane);
         }
-    } else if (W == 3) {
-        if constexpr (NWMAX >= 6) serve_slot<6>(a, i, slot, in, base, lane);
+    } else if (W == 3) {  // five 32-bit words up to N = 160
+        if constexpr (NWMAX >= 6) {
+            if (in.N <= 160)
+                serve_slot<5>(a, i, slot, in, base, lane);
+            else
+                serve_slot<6>(a, i, slot, in, base, lane);
+        }
     } else {
         if constexpr (NWMAX >= 8) serve_slot<8>(a, i, slot, in, base, lane);
     }

@@ -99,15 +99,16 @@ struct PlaneMax {
 // so n words cost about n/2 + log n popcounts instead of n.  The adders
 // trade popcounts (XU pipe) for logic (ALU pipe), which pays while the
 // step has registers to spare: for 7 or more words (six- and eight-word
-// sequences, N > 128) plain popcounts measured 14-21 % faster on GB300
-// and 2-16 % slower below.  Five words (four-word sequences) take one
-// full adder and two plain popcounts, about 1 % faster than two adders.
+// sequences, N > 160) plain popcounts measured 14-21 % faster on GB300
+// and 2-16 % slower below; five-word sequences (6 words) count plainly as
+// well.  Five words (four-word sequences) take one full adder and two plain
+// popcounts, about 1 % faster than two adders.
 template <int n, int weight>
 __device__ __forceinline__ int csa_popc(const uint32_t (&w)[n]) {
     if constexpr (weight == 1 && n == 5) {
         const uint32_t a = w[0], b = w[1], c = w[2];
         return __popc(a ^ b ^ c) + 2 * __popc((a & b) | (c & (a | b))) + __popc(w[3]) + __popc(w[4]);
-    } else if constexpr (n <= 2 || (weight == 1 && n >= 7)) {
+    } else if constexpr (n <= 2 || (weight == 1 && n >= 6)) {
         int s = 0;
 #pragma unroll
         for (int i = 0; i < n; ++i) s += __popc(w[i]);
