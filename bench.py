@@ -150,10 +150,22 @@ def cpu_baseline_run(replicas: int, threads: int, steps: int, n: int | None = No
                       f"{steps} tabu steps each, one replica per thread, {dt:.1f} s wall"}
 
 
+def apply_overrides(args) -> None:
+    """--n, --replicas and --steps-per-replica resize the default workload (both arms)."""
+    global N, WORKLOAD, REPLICAS, STEPS_PER_REPLICA
+    if args.n:
+        N, WORKLOAD = args.n, f"replicas_n{args.n}"
+    if args.replicas:
+        REPLICAS = args.replicas
+    if args.steps_per_replica:
+        STEPS_PER_REPLICA = args.steps_per_replica
+
+
 def run_reference(args) -> None:
     world, rank, _ = dist_env()
     if rank != 0:
         return
+    apply_overrides(args)
     cores = cpu_cores()
     for _ in range(args.warmup):
         cpu_baseline_run(cores, cores, STEPS_PER_REPLICA // 10)
@@ -203,13 +215,7 @@ def run_gpu(args) -> None:
             pg.barrier()
         torch.cuda.synchronize()
 
-    global N, WORKLOAD, REPLICAS, STEPS_PER_REPLICA
-    if args.n:
-        N, WORKLOAD = args.n, f"replicas_n{args.n}"
-    if args.replicas:
-        REPLICAS = args.replicas
-    if args.steps_per_replica:
-        STEPS_PER_REPLICA = args.steps_per_replica
+    apply_overrides(args)
     first, _ = parallel.shard(world, rank, REPLICAS)
     P = labs.make_params(N, K, max_steps=STEPS_PER_REPLICA)
     out = torch.empty((REPLICAS, 8), dtype=torch.int64, device=dev)
