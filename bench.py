@@ -611,6 +611,73 @@ def run_skew_ab(args) -> None:
             "per_N": per_n}), flush=True)
 
 
+def table2_energy(n: int) -> int:
+    """The lowest energy Table II prints for N (tests/golden/table2_new_records.txt)."""
+    best = None
+    with open(os.path.join(ROOT, "tests", "golden", "table2_new_records.txt")) as f:
+        for line in f:
+            parts = line.split()
+            if parts and not line.startswith("#") and int(parts[0]) == n:
+                best = int(parts[1]) if best is None else min(best, int(parts[1]))
+    if best is None:
+        raise SystemExit(f"Table II has no entry for N={n}")
+    return best
+
+
+def run_record(args) -> None:
+    """A record search as the paper runs them (Sec. IV), bounded in time: 16
+    replicas per SM with the global termination flag race to Table II's energy
+    for N, in slices of generations continued with labs_mts_resume (so a search
+    can be stopped and resumed at any slice).  Populations stagnate after some
+    seconds, so every --record-epoch-s the search restarts with fresh replicas
+    (the next block of instance numbers).  Reports the best E over time and the
+    time to the target if it is reached within --record-seconds."""
+    torch, dev, pg, world, rank = gpu_context(args)
+    import paper_2504_00987_gb300 as labs
+
+    n = args.record_n
+    target = table2_energy(n)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    reps = args.replicas or sms * 16
+    K, seed = 100, 2025
+    state = torch.empty(reps * labs.mts_state_bytes(n, K), dtype=torch.uint8, device=dev)
+    flag = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = torch.empty((reps, 8), dtype=torch.int64, device=dev)
+    gens, history, reached_s, best, steps, epoch = 500, [], None, None, 0, 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < args.record_seconds and reached_s is None:
+        first, G, t_epoch = epoch * reps, 0, time.perf_counter()
+        while (time.perf_counter() - t_epoch < args.record_epoch_s
+               and time.perf_counter() - t0 < args.record_seconds):
+            G += gens
+            P = labs.make_params(n, K, max_generations=G, target_E=target, glf=True)
+            labs.mts_resume(P, seed, first, reps, state, resume=G > gens, out=out, glf_flag=flag)
+            res = labs.decode_results(out, n, first)
+            elapsed = time.perf_counter() - t0
+            b = min(res, key=lambda r: (r["E"], r["instance"]))
+            if best is None or b["E"] < best["E"]:
+                best = b
+                history.append({"s": round(elapsed, 3), "E": b["E"], "epoch": epoch, "generations": G})
+            if any(r["status"] == labs.RUN_REACHED for r in res):
+                reached_s = elapsed
+                break
+        steps += sum(r["steps"] for r in res)
+        epoch += 1
+    if rank == 0:
+        print(json.dumps({
+            "metric": "best E within the time budget", "value": best["E"], "unit": "E", "n_gpus": world,
+            "higher_is_better": False, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"record_n{n}: {reps} replicas, K={K}, seed {seed}, target = Table II E "
+                                   f"{target}, slices of {gens} generations, fresh replicas every "
+                                   f"{args.record_epoch_s} s, budget {args.record_seconds} s"},
+            "epochs": epoch,
+            "target_E": target, "reached": reached_s is not None, "time_to_target_s": reached_s,
+            "best_merit_factor": n * n / (2.0 * best["E"]), "best_instance": best["instance"],
+            "best_seq_words": best["seq"], "tabu_steps": steps, "flip_evals_per_s": steps * n / (time.perf_counter() - t0),
+            "history": history}), flush=True)
+
+
 def run_batch(args) -> None:
     """512 uneven instances (N ~ U{40..127}, K ~ U{50..200}, 10 N^2 steps) in one autotuned,
     graph-captured persistent launch vs one launch per instance."""
@@ -799,7 +866,7 @@ def main() -> None:
     ap.add_argument("--steps-per-replica", type=int, default=0, help="profiling only: override budget")
     ap.add_argument("--n", type=int, default=0, help="profiling only: override N of the default workload")
     ap.add_argument("--workload", choices=["replicas_n64", "sweep_n92_120", "tts", "tts_ab", "skew_ab", "batch",
-                                           "serve", "skew"],
+                                           "serve", "skew", "record"],
                     default="replicas_n64")
     ap.add_argument("--runs", type=int, default=50, help="tts: runs per N")
     ap.add_argument("--tts-n", default="", help="tts: comma-separated N (default: all; tts_ab: first five)")
@@ -807,6 +874,9 @@ def main() -> None:
                     help="tts: oracle one-minute best (N=92..120) or exact optimum (N=16..36)")
     ap.add_argument("--fit-min-n", type=int, default=30,
                     help="tts: smallest N of the second steps fit (above the one-generation floor)")
+    ap.add_argument("--record-n", type=int, default=92, help="record: N (a Table II length)")
+    ap.add_argument("--record-seconds", type=float, default=120.0, help="record: time budget")
+    ap.add_argument("--record-epoch-s", type=float, default=10.0, help="record: seconds before fresh replicas")
     ap.add_argument("--requests", type=int, default=20_000, help="serve: requests")
     ap.add_argument("--baseline-requests", type=int, default=400, help="serve: plain-form prefix")
     ap.add_argument("--slots", type=int, default=0, help="serve: resident slots")
@@ -826,6 +896,8 @@ def main() -> None:
         run_tts_ab(args)
     elif args.workload == "skew_ab":
         run_skew_ab(args)
+    elif args.workload == "record":
+        run_record(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "serve":
