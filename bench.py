@@ -639,7 +639,7 @@ def run_record(args) -> None:
     target = table2_energy(n)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     reps = args.replicas or sms * 16
-    K, seed = 100, 2025
+    K, seed = 100, args.record_seed
     state = torch.empty(reps * labs.mts_state_bytes(n, K), dtype=torch.uint8, device=dev)
     flag = torch.zeros(1, dtype=torch.int32, device=dev)
     out = torch.empty((reps, 8), dtype=torch.int64, device=dev)
@@ -877,6 +877,7 @@ def main() -> None:
     ap.add_argument("--record-n", type=int, default=92, help="record: N (a Table II length)")
     ap.add_argument("--record-seconds", type=float, default=120.0, help="record: time budget")
     ap.add_argument("--record-epoch-s", type=float, default=10.0, help="record: seconds before fresh replicas")
+    ap.add_argument("--record-seed", type=int, default=2025, help="record: Philox seed")
     ap.add_argument("--requests", type=int, default=20_000, help="serve: requests")
     ap.add_argument("--baseline-requests", type=int, default=400, help="serve: plain-form prefix")
     ap.add_argument("--slots", type=int, default=0, help="serve: resident slots")
