@@ -154,3 +154,38 @@ def test_serve_argument_errors_without_gpu(lib):
     assert ctypes.sizeof(nat.ServeOpts) == 4 * 4 + 8 * 5
     assert lib.labs_serve_destroy(None) == nat.LABS_OK
     assert lib.labs_serve_poll(None, 1, None) == nat.LABS_EINVAL
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes mirror has the size and field offsets the C compiler gives
+    the struct of include/labs.h (a C program compiled here prints them)."""
+    import shutil
+    import subprocess
+
+    from paper_2504_00987_gb300 import _native as nat
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    pairs = [("labs_params", nat.Params), ("labs_device_result", nat.DeviceResult),
+             ("labs_result", nat.Result), ("labs_tabu_opts", nat.TabuOpts), ("labs_instance", nat.Instance),
+             ("labs_mapping", nat.Mapping), ("labs_serve_opts", nat.ServeOpts),
+             ("labs_serve_stats", nat.ServeStats)]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "labs.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append(f'    printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    include = os.path.join(ROOT, "include")
+    subprocess.check_call(["gcc", "-std=c11", "-I", include, "-o", str(exe), str(src)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        cname, what, value = line.split()
+        got[(cname, what)] = int(value)
+    for cname, py in pairs:
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
