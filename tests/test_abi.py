@@ -189,3 +189,13 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_every_entry_point_has_declared_ctypes_types(lib):
+    """No call goes through ctypes' default int conversion (64-bit arguments
+    would be truncated): every exported function has argtypes and restype."""
+    from paper_2504_00987_gb300 import _native as nat
+
+    for name in nat.EXPORTED:
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None and fn.restype is not None, name
