@@ -7,7 +7,7 @@ namespace lgpu {
 
 size_t mts_smem_per_warp(int N, int K) {
     const int NW = 2 * ((N + 63) / 64);
-    const size_t bytes = static_cast<size_t>(K) * NW * 4 + static_cast<size_t>(K) * 4 + 32u * NW * 4;
+    const size_t bytes = static_cast<size_t>(K) * NW * 4 + static_cast<size_t>(K) * 4 + 64u * NW * 4;
     return (bytes + 15) & ~static_cast<size_t>(15);
 }
 

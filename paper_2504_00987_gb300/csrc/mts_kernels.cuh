@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) mts_resume_kernel(const R
 
 template <int NW, bool TRACE, bool SKEW>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) tabu_kernel(const TabuArgs a) {
-    __shared__ int32_t Cs_all[kWarpsPerBlock][32 * NW];
+    __shared__ int32_t Cs_all[kWarpsPerBlock][64 * NW];  // two buffers of C_k
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int64_t b = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + warp;

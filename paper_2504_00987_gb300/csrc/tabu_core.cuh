@@ -237,11 +237,47 @@ __device__ __forceinline__ int plane_count(const int32_t (&c)[NW]) {
     return 33 - __clz(__reduce_max_sync(kFull, mx));
 }
 
+// The lane's windows of an NW-word vector: XB[i] = word i of B >> lane and
+// YB[i] = word i of RL >> (31 - lane).  For j = lane + 32q, word w of the
+// forward window X_j (bit k = b_{j+k}) is XB[q + w] and word w of the
+// backward window Y_j (bit k = b_{j-k}) is YB[w + NW - 1 - q]; both are zero
+// past the ends of the sequence.
+template <int NW>
+__device__ __forceinline__ void pivot_windows(const uint32_t (&B)[NW], const uint32_t (&RL)[NW],
+                                              int lane, uint32_t (&XB)[NW], uint32_t (&YB)[NW]) {
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+        XB[i] = __funnelshift_r(B[i], i + 1 < NW ? B[i + 1] : 0u, lane);
+        YB[i] = __funnelshift_r(RL[i], i + 1 < NW ? RL[i + 1] : 0u, 31 - lane);
+    }
+}
+
 // One tabu search from `seq` (warp-uniform).  On return `seq` holds
 // bestSeqTS.  Draws: step t uses Philox(instance, g, t, 4): x tie, y tenure.
 // FIX_FIRST: bit 0 (s_1) is never a candidate move.
-// `Cs` is warp-private shared scratch of 32*NW ints.  With TRACE, `trace`
-// receives {g, t, j, E} per step while trace_len < trace_cap.
+// `Cs` is warp-private shared scratch of 64*NW ints (two buffers of C_k).
+// With TRACE, `trace` receives {g, t, j, E} per step while trace_len <
+// trace_cap.
+//
+// Neighbour scores are kept between steps.  With
+//   R_j = sum_k C_k (s~_{j+k} + s~_{j-k})     (s~_i = s_i inside 0..N-1, else 0)
+//   M_j = sum_{k>=1} s~_{j+k} s~_{j-k},
+// the energy after flipping j is E_j = E + 4(N-1) + 8 M_j - 4 s_j R_j (the
+// delta_k(j)(2 C_k + delta_k(j)) sum of Table I, expanded).  R_j is set up
+// once per search on the bit planes of C_k; after the move p (s_p before
+// it, C and C' the correlations before and after, d = |p - j|) it changes
+// exactly by
+//   R'_j = R_j - 2 s_p (C_d + C'_d + F_j) - 2 s_j          (j != p)
+//   R'_p = R_p - 2 s_p (N - 1 + 2 M_p)
+// with F_j = sum_{k>=1} s~_{p+k} s~'_{j-k} + sum_{k>=1} s~_{p-k} s~'_{j+k}
+// (s~' after the move).  Derivation: R'_j - R_j = sum_k C_k (s~'-s~)
+// (terms j+-k = p: -2 s_p C_d) + sum_k delta_k(p) (s~'_{j+k} + s~'_{j-k});
+// the second sum pairs the windows of p and j: its same-direction pairs
+// (p+k, j+k), (p-k, j-k) cover every product of C'_d except s'_p s'_j, and
+// its crossed pairs are F_j.  F_j is two masked popcounts over the windows
+// of p and j (the crossed pairs agree or disagree), C_d and C'_d are read
+// from the two shared buffers, so a step costs about one bit plane of the
+// from-scratch scoring instead of one per bit of max |C_k|.
 template <int NW, bool TRACE, bool FIX_FIRST = false>
 __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key,
                                const uint32_t inst, const uint32_t g, const int max_iter,
@@ -249,9 +285,9 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
                                int4* __restrict__ trace, const int64_t trace_cap,
                                int64_t& trace_len, const int lane) {
     constexpr int NB = 32 * NW;
-    // Correlations are recomputed from the pivot after every move when the
-    // windows are short (cheaper on the ALU pipe than the per-k update),
-    // and updated incrementally otherwise.
+    // Correlations after a move are recomputed from the pivot's windows when
+    // they are short (fewer ALU-pipe instructions than the per-k update) and
+    // updated per k otherwise.
     constexpr bool kRecompute = NW <= 4;
     uint32_t B[NW], RL[NW], Bb[NW];
 #pragma unroll
@@ -259,7 +295,9 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
         B[w] = seq[w];
         Bb[w] = seq[w];
     }
-    reverse_bits<NW>(B, RL);  // bit (NB-1-i) of RL = b_i
+    reverse_bits<NW>(B, RL);
+    uint32_t XB[NW], YB[NW];
+    pivot_windows<NW>(B, RL, lane, XB, YB);
     int32_t c[NW];
     correlations<NW>(B, N, lane, c);
     int32_t E;
@@ -270,45 +308,72 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
         E = __reduce_add_sync(kFull, sq);
     }
     int32_t E_best = E;
-    // Per-search constants of the lane's neighbours j = lane + 32q: the
-    // parity plane of C_k (bit k set iff 1 <= k <= N-1 and N - k odd), the
-    // masks of k in [1, L_j] with L_j = min(j, N-1-j) used by M_j, L_j, and
-    // the mirror index N-1-j of T_j.
-    uint32_t par[NW];
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        const uint32_t alt = ((N - 32 * w) & 1) ? 0x55555555u : 0xAAAAAAAAu;  // (N - k) odd
-        par[w] = alt & word_lowmask(w, N) & (w == 0 ? ~1u : kFull);
-    }
-    int32_t tabu[NW], Lq[NW], mir[NW];
-    uint32_t mmask[NW][NW];
-    uint32_t jvalid = 0;  // bit q: j < N
+    // Per-search constants of the lane's neighbours j = lane + 32q: validity,
+    // L_j = min(j, N-1-j) and the masks of k in [1, L_j] (M_j), the range
+    // masks of the forward windows (bits k <= N-1-j of X_j, word i = q + w),
+    // and for the recomputed correlations the masks of i < N - k.
+    int32_t tabu[NW], Lq[NW];
+    uint32_t mmask[NW][NW], mX[NW];
+    uint32_t jvalid = 0;  // bit q: j < N and j may move
 #pragma unroll
     for (int q = 0; q < NW; ++q) {
         tabu[q] = 0;
         const int j = lane + 32 * q;
         Lq[q] = min(j, N - 1 - j);
-        mir[q] = j < N ? N - 1 - j : 0;
         jvalid |= (j < N && !(FIX_FIRST && j == 0) ? 1u : 0u) << q;
+        mX[q] = word_lowmask(q, N - lane);
 #pragma unroll
         for (int w = 0; w <= q && w + q < NW; ++w)
             mmask[q][w] = word_lowmask(w, Lq[q] + 1) & (w == 0 ? ~1u : kFull);
+    }
+    const uint32_t low_l = (lane == 31) ? kFull : ((2u << lane) - 1u);  // bits 0..lane
+    // R_j = 2 S_j - T_j from the bit planes of C_k (S_j) and the prefix sums
+    // of C_k (T_j = PC(j) + PC(N-1-j)), once per search.
+    int32_t R[NW];
+    {
+        uint32_t par[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t alt = ((N - 32 * w) & 1) ? 0x55555555u : 0xAAAAAAAAu;  // (N - k) odd
+            par[w] = alt & word_lowmask(w, N) & (w == 0 ? ~1u : kFull);
+        }
+        uint32_t X[NW][NW], Y[NW][NW];
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+#pragma unroll
+            for (int w = 0; w + q < NW; ++w) X[q][w] = XB[q + w];
+#pragma unroll
+            for (int w = 0; w <= q; ++w) Y[q][w] = YB[w + NW - 1 - q];
+        }
+        int32_t S[NW], pc[NW], T[NW];
+        score_dispatch<NW>(plane_count<NW>(c), c, par, X, Y, S);
+        prefix_own<NW>(c, lane, pc);
+        mirror_terms<NW>(pc, N, lane, Cs, T);
+#pragma unroll
+        for (int q = 0; q < NW; ++q) R[q] = 2 * S[q] - T[q];
+    }
+    int32_t* Ccur = Cs;       // C_k of the pivot, k = 0 .. NB-1 (C_0 = 0)
+    int32_t* Cnxt = Cs + NB;  // C_k after the move
+#pragma unroll
+    for (int q = 0; q < NW; ++q) Ccur[lane + 32 * q] = c[q];
+    __syncwarp();
+    // correlation masks of the recomputation: i < N - k for k = lane + 32q
+    uint32_t cmask[kRecompute ? NW : 1][kRecompute ? NW : 1];
+    int32_t nk[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        const int k = lane + 32 * q;
+        nk[q] = (k >= 1 && k <= N - 1) ? N - k : 0;
+        if constexpr (kRecompute) {
+#pragma unroll
+            for (int w = 0; w + q < NW; ++w) cmask[q][w] = word_lowmask(w, nk[q]);
+        }
     }
     const int min_t = max_iter / 10;
     const int max_t = (12 * max_iter) / 100;
     const int64_t nsteps = budget < 0 ? max_iter : (budget < max_iter ? budget : max_iter);
     uint32_t rx = 0, ry = 0;
     int64_t steps = 0;
-    int P = plane_count<NW>(c);
-    int32_t pc[NW], T[NW];
-    prefix_own<NW>(c, lane, pc);
-#pragma unroll
-    for (int q = 0; q < NW; ++q) Cs[lane + 32 * q] = pc[q];
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < NW; ++q) T[q] = pc[q] + Cs[mir[q]];
-    __syncwarp();
-    const uint32_t low_l = (lane == 31) ? kFull : ((2u << lane) - 1u);  // bits 0..lane
 
     for (int t = 1; t <= nsteps; ++t) {
         if (((t - 1) & 31) == 0) {  // draws of steps t .. t+31, one per lane
@@ -319,125 +384,114 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
         const int src = (t - 1) & 31;
         const uint32_t u_tie = __shfl_sync(kFull, rx, src);
         const uint32_t u_ten = __shfl_sync(kFull, ry, src);
-        // ---- windows X_j = B >> j and Y_j (bit k = b_{j-k}) for j = lane + 32q
-        uint32_t X[NW][NW], Y[NW][NW];
-#pragma unroll
-        for (int q = 0; q < NW; ++q) {
-#pragma unroll
-            for (int w = 0; w + q < NW; ++w)
-                X[q][w] = __funnelshift_r(B[w + q], (w + q + 1 < NW) ? B[w + q + 1] : 0u, lane);
-#pragma unroll
-            for (int w = 0; w <= q; ++w)
-                Y[q][w] = __funnelshift_r(RL[w + NW - 1 - q], (w + NW - q < NW) ? RL[w + NW - q] : 0u,
-                                          31 - lane);
-        }
-        // ---- S_j on the bit planes of C_k (T_j is kept up to date by the moves)
-        int32_t S[NW];
-        score_dispatch<NW>(P, c, par, X, Y, S);
-        // ---- E_j, admissibility (tabu expired or aspiration), candidates
+        // ---- E_j for j = lane + 32q, admissibility, packed (E_j, j) keys
         const int32_t E0 = E + 4 * (N - 1);
-        int32_t cand[NW];
-        int32_t lmin = INT_MAX;
+        int32_t cand[NW], Mq[NW];
+        int32_t kmin_l = INT_MAX;
 #pragma unroll
         for (int q = 0; q < NW; ++q) {
             int dm = 0;
 #pragma unroll
-            for (int w = 0; w <= q && w + q < NW; ++w) dm += __popc((X[q][w] ^ Y[q][w]) & mmask[q][w]);
-            const int32_t M = Lq[q] - 2 * dm;
-            const int32_t V = 2 * S[q] - T[q];
-            const int32_t sv = (X[q][0] & 1u) ? V : -V;  // s_j (2 S_j - T_j); bit 0 of X_j is b_j
-            const int32_t Ej = E0 + 8 * M - 4 * sv;
+            for (int w = 0; w <= q && w + q < NW; ++w)
+                dm += __popc((XB[q + w] ^ YB[w + NW - 1 - q]) & mmask[q][w]);
+            Mq[q] = Lq[q] - 2 * dm;
+            const int32_t sR = (XB[q] & 1u) ? R[q] : -R[q];  // s_j R_j; bit 0 of X_j is b_j
+            const int32_t Ej = E0 + 8 * Mq[q] - 4 * sR;
             const bool adm = ((jvalid >> q) & 1u) && (tabu[q] < t || Ej < E_best);
             cand[q] = adm ? Ej : INT_MAX;
-            lmin = min(lmin, cand[q]);
+            // E_j < 2^23 for N <= 256 and j < 256: (E_j, j) packs into 31 bits
+            kmin_l = min(kmin_l, adm ? (Ej << 8) | (lane + 32 * q) : INT_MAX);
         }
-        const int32_t m = __reduce_min_sync(kFull, lmin);
-        if (m == INT_MAX) break;  // unreachable: maxTabu < N leaves a bit free
-        uint32_t tb[NW];
-        int count = 0;
+        const int32_t kmin = __reduce_min_sync(kFull, kmin_l);
+        if (kmin == INT_MAX) break;  // every move tabu and none aspirates
+        const int32_t m = kmin >> 8;
+        int p = kmin & 255;  // lowest admissible minimiser
+        {
+            int eq = 0;
 #pragma unroll
-        for (int q = 0; q < NW; ++q) {
-            tb[q] = __ballot_sync(kFull, cand[q] == m);
-            count += __popc(tb[q]);
-        }
-        // lowest admissible minimiser; it is the pick whenever the tie draw selects index 0
-        int lj = INT_MAX;
+            for (int q = 0; q < NW; ++q) eq += (cand[q] == m) ? 1 : 0;
+            const int count = __reduce_add_sync(kFull, eq);
+            int idx = count > 1 ? static_cast<int>((static_cast<uint64_t>(u_tie) * count) >> 32) : 0;
+            if (idx > 0) {  // the idx-th minimiser in ascending j
+                bool found = false;
 #pragma unroll
-        for (int q = NW - 1; q >= 0; --q)
-            if (cand[q] == m) lj = lane + 32 * q;
-        int p = __reduce_min_sync(kFull, lj);
-        int idx = count > 1 ? static_cast<int>((static_cast<uint64_t>(u_tie) * count) >> 32) : 0;
-        if (idx > 0) {
-            bool found = false;
-#pragma unroll
-            for (int q = 0; q < NW; ++q) {
-                const int pc_q = __popc(tb[q]);
-                if (!found) {
-                    if (idx < pc_q) {
-                        p = 32 * q + nth_set_bit(tb[q], idx);
-                        found = true;
-                    } else {
-                        idx -= pc_q;
+                for (int q = 0; q < NW; ++q) {
+                    const uint32_t tb = __ballot_sync(kFull, cand[q] == m);
+                    const int pc_q = __popc(tb);
+                    if (!found) {
+                        if (idx < pc_q) {
+                            p = 32 * q + nth_set_bit(tb, idx);
+                            found = true;
+                        } else {
+                            idx -= pc_q;
+                        }
                     }
                 }
             }
         }
-        // ---- apply: windows of the move, C_k, PC(n), flip, tenure, bestSeqTS
-        uint32_t Xp[NW], Yp[NW];  // bit k = b_{p+k} and b_{p-k}
-        if constexpr (NW >= 4) {
-            // the windows of j = p, fetched from the lane that owns p (cheaper
-            // than shifting the pivot when the shift network is deep)
-            const int qp = p >> 5, lp = p & 31;
+        // ---- the move p: its windows (before the flip; bits k >= 1 are the
+        // same after it), s_p, and the ranges k in [1, N-1-p] and [1, p]
+        uint32_t Xp[NW], Yp[NW], mu[NW], mv[NW];
+        shr_uniform<NW>(B, p, Xp);
+        shr_uniform<NW>(RL, NB - 1 - p, Yp);
+        const int32_t sp2 = (Xp[0] & 1u) ? 2 : -2;  // 2 s_p
 #pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                uint32_t xs = 0, ys = 0;
-#pragma unroll
-                for (int q = 0; q < NW; ++q) {
-                    if (w + q < NW) xs = (q == qp) ? X[q][w] : xs;
-                    if (w <= q) ys = (q == qp) ? Y[q][w] : ys;
-                }
-                Xp[w] = __shfl_sync(kFull, xs, lp);
-                Yp[w] = __shfl_sync(kFull, ys, lp);
-            }
-        } else {
-            shr_uniform<NW>(B, p, Xp);
-            shr_uniform<NW>(RL, NB - 1 - p, Yp);
+        for (int w = 0; w < NW; ++w) {
+            mu[w] = word_lowmask(w, N - p) & (w == 0 ? ~1u : kFull);
+            mv[w] = word_lowmask(w, p + 1) & (w == 0 ? ~1u : kFull);
         }
-        const int32_t sp2 = (Xp[0] & 1u) ? 2 : -2;
+        int32_t dq[NW], c0[NW];
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+            dq[q] = abs(p - (lane + 32 * q));
+            c0[q] = Ccur[dq[q]];  // C_d before the move
+        }
         flip_bit<NW>(B, p);
         flip_bit<NW>(RL, NB - 1 - p);
+        pivot_windows<NW>(B, RL, lane, XB, YB);
         if constexpr (kRecompute) {
-            correlations<NW>(B, N, lane, c);
+#pragma unroll
+            for (int q = 0; q < NW; ++q) {
+                int cnt = 0;
+#pragma unroll
+                for (int w = 0; w + q < NW; ++w) cnt += __popc((B[w] ^ XB[w + q]) & cmask[q][w]);
+                c[q] = nk[q] - 2 * cnt;
+            }
         } else {
 #pragma unroll
             for (int q = 0; q < NW; ++q) {
-                const int k = lane + 32 * q;
                 const int32_t bx = (Xp[q] >> lane) & 1u, by = (Yp[q] >> lane) & 1u;
-                const int32_t sx = (k >= 1 && k + p <= N - 1) ? 2 * bx - 1 : 0;
-                const int32_t sy = (k >= 1 && k <= p) ? 2 * by - 1 : 0;
+                const int32_t sx = ((mu[q] >> lane) & 1u) ? 2 * bx - 1 : 0;
+                const int32_t sy = ((mv[q] >> lane) & 1u) ? 2 * by - 1 : 0;
                 c[q] -= sp2 * (sx + sy);
             }
         }
-        P = plane_count<NW>(c);  // for the next step; overlaps with the tail below
-        // PC(n) += sum_{k=1}^{n} delta_k(p)
-        //       = -2 s_p [2 (#ones of b_{p+k}, b_{p-k} for k in 1..n) - min(n, N-1-p) - min(n, p)]
-        {
-            const int32_t bp = static_cast<int32_t>(Xp[0] & 1u);  // bit 0 of both windows is b_p
-            int32_t ux = 0;                                         // ones in whole words below q
 #pragma unroll
-            for (int q = 0; q < NW; ++q) {
-                const int n = lane + 32 * q;
-                const int32_t ones = ux + __popc(Xp[q] & low_l) + __popc(Yp[q] & low_l) - 2 * bp;
-                pc[q] -= sp2 * (2 * ones - min(n, N - 1 - p) - min(n, p));
-                if (q + 1 < NW) ux += __popc(Xp[q]) + __popc(Yp[q]);
-            }
+        for (int q = 0; q < NW; ++q) Cnxt[lane + 32 * q] = c[q];
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+            const int j = lane + 32 * q;
+            const int32_t c1 = Cnxt[dq[q]];  // C'_d
+            // crossed pairs: (p+k, j-k) for k <= min(N-1-p, j) and
+            // (p-k, j+k) for k <= min(p, N-1-j); each disagreement is -1
+            uint32_t words[NW + 1];
+#pragma unroll
+            for (int w = 0; w <= q; ++w)
+                words[w] = (Xp[w] ^ YB[w + NW - 1 - q]) & mu[w] & (w == q ? low_l : kFull);
+#pragma unroll
+            for (int w = 0; w + q < NW; ++w) words[q + 1 + w] = (Yp[w] ^ XB[q + w]) & mv[w] & mX[q + w];
+            const int32_t F = min(N - 1 - p, j) + min(p, N - 1 - j) - 2 * csa_popc<NW + 1, 1>(words);
+            const int32_t sj2 = (XB[q] & 1u) ? 2 : -2;
+            const int32_t Rj = R[q] - sp2 * (c0[q] + c1 + F) - sj2;
+            const int32_t Rp = R[q] - sp2 * (N - 1 + 2 * Mq[q]);
+            R[q] = (j == p) ? Rp : Rj;
         }
-#pragma unroll
-        for (int q = 0; q < NW; ++q) Cs[lane + 32 * q] = pc[q];
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < NW; ++q) T[q] = pc[q] + Cs[mir[q]];
-        __syncwarp();
+        {
+            int32_t* tmp = Ccur;
+            Ccur = Cnxt;
+            Cnxt = tmp;
+        }
         const int32_t expiry = t + rand_int(min_t, max_t, u_ten);
 #pragma unroll
         for (int q = 0; q < NW; ++q)
@@ -456,6 +510,7 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
             }
         }
     }
+    __syncwarp();  // the buffers are reused by the caller
 #pragma unroll
     for (int w = 0; w < NW; ++w) seq[w] = Bb[w];
     TabuOut out;
