@@ -252,6 +252,20 @@ int32_t labs_mts_run(const labs_params* P, uint64_t seed, uint64_t first_instanc
                      int64_t replicas, labs_result* h_out, labs_stream_t stream);
 
 /*
+ * labs_results_decode -- the host form of device result records (from
+ * labs_mts_launch or labs_mts_resume, copied to host memory by the caller):
+ * h_out[r] gets the record's sequence, E, status and counters, the merit
+ * factor F = N^2 / (2E) of Eq. 3 (0 when E <= 0), flip_evals = steps * N,
+ * instance = first_instance + r and seconds = 0.  E is copied with its
+ * sign: a record refused by labs_mts_resume (LABS_RUN_BADSTATE) carries
+ * E = -1.  Host memory only (h_in: n records, h_out: n results, both owned
+ * by the caller); touches no GPU.  LABS_EINVAL for N outside 3..LABS_MAX_N,
+ * n < 0, or a NULL buffer with n > 0.
+ */
+int32_t labs_results_decode(const labs_device_result* h_in, int64_t n, int32_t N,
+                            uint64_t first_instance, labs_result* h_out);
+
+/*
  * Checkpoint and resume.  Between two generations a replica's whole state
  * is its population, their energies, its best sequence and its generation
  * and step counters: every later draw is addressed by (instance,
@@ -417,9 +431,12 @@ int32_t labs_serve_destroy(labs_server* s);
  * the library, sized for LABS_STATIC_MAX_REPLICAS replicas (about 256 KiB),
  * which every GPU that loads the library holds until the process exits.
  *   - replicas > LABS_STATIC_MAX_REPLICAS is rejected with LABS_EINVAL.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress,
+ *     a host-side query that allocates nothing) with the caller's device
+ *     current, so the address stays right after cudaDeviceReset.  The first
+ *     call on a device (and the first after a reset) loads the library's
+ *     device code, which places the array: make it before any stream
+ *     capture.
  *   - All calls on a device share the one array, which keeps the last
  *     call's contents (each call clears the flag and overwrites the records
  *     it reads): calls whose GPU work overlaps -- on different streams or

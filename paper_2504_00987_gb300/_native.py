@@ -41,7 +41,7 @@ EXPORTED = [
     "labs_batch_destroy", "labs_mts_batch_run", "labs_mts_run_static", "labs_serve_create",
     "labs_serve_submit", "labs_serve_poll", "labs_serve_cancel", "labs_serve_stats_get",
     "labs_serve_destroy", "labs_skew_deviation_batch", "labs_philox_batch",
-    "labs_mts_state_bytes", "labs_mts_resume",
+    "labs_mts_state_bytes", "labs_mts_resume", "labs_results_decode",
 ]
 STATIC_MAX_REPLICAS = 4096
 VARIANT_UNIFORM_CROSSOVER = 1
@@ -238,6 +238,8 @@ def load(path: str = LIB_PATH):
         L.labs_mts_resume.argtypes = [ctypes.POINTER(Params), u64, u64, i64, vp, i32, vp, vp, vp]
         L.labs_philox_batch.restype = i32
         L.labs_philox_batch.argtypes = [u64, vp, i64, vp, vp]
+        L.labs_results_decode.restype = i32
+        L.labs_results_decode.argtypes = [vp, i64, i32, u64, RP]
         L.labs_mts_run_static.restype = i32
         L.labs_mts_run_static.argtypes = [ctypes.POINTER(Params), u64, u64, i64, RP, vp]
         _lib = L

@@ -145,27 +145,15 @@ def mts_resume(params: nat.Params, seed: int, first_instance: int, replicas: int
 
 
 def decode_results(out: torch.Tensor, N: int, first_instance: int = 0) -> list[dict]:
-    """labs_device_result rows (from mts_launch) -> dicts, on the host."""
-    h = out.detach().cpu()
-    rows = []
-    W = words_for(N)
-    for r in range(h.shape[0]):
-        row = h[r].tolist()
-        packed = row[4] & 0xFFFFFFFFFFFFFFFF
-        E = packed & 0xFFFFFFFF
-        status = (packed >> 32) & 0xFFFFFFFF
-        rows.append({
-            "instance": first_instance + r,
-            "seq": [w & 0xFFFFFFFFFFFFFFFF for w in row[:W]],
-            "E": E,
-            "F": N * N / (2.0 * E) if E > 0 else 0.0,
-            "status": status,
-            "generations": row[5],
-            "steps": row[6],
-            "flip_evals": row[6] * N,
-            "trace_len": row[7],
-        })
-    return rows
+    """labs_device_result rows (from mts_launch / mts_resume) -> dicts, decoded on
+    the host by labs_results_decode (merit factor, flip evaluations)."""
+    h = out.detach().to("cpu").contiguous()
+    if h.dtype != torch.int64 or h.dim() != 2 or h.shape[1] != 8:
+        raise ValueError("device results must be an (n, 8) int64 tensor")
+    n = h.shape[0]
+    res = (nat.Result * max(n, 1))()
+    nat.check(nat.load().labs_results_decode(ctypes.c_void_p(h.data_ptr()), n, N, first_instance, res))
+    return _result_dicts(res, n, with_N=False)
 
 
 def mts_run(params: nat.Params, seed: int, first_instance: int, replicas: int, stream=None) -> list[dict]:

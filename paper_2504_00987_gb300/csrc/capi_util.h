@@ -10,6 +10,10 @@
 
 #include "labs.h"
 
+namespace lgpu {
+struct MtsArgs;
+}
+
 namespace lcapi {
 
 int32_t fail(int32_t code, const char* fmt, ...);
@@ -35,6 +39,10 @@ struct NvtxRange {
     NvtxRange(const NvtxRange&) = delete;
     NvtxRange& operator=(const NvtxRange&) = delete;
 };
+// Validates P and fills the Memetic-Tabu kernel arguments of labs_mts_launch,
+// labs_mts_run and labs_mts_run_static (everything except the device pointers).
+int32_t make_mts_args(const labs_params* P, uint64_t seed, uint64_t first_instance,
+                      int64_t replicas, lgpu::MtsArgs* a);
 void fill_host_result(const labs_device_result& d, int32_t N, uint64_t instance, double seconds,
                       labs_result* o);
 

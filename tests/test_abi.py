@@ -199,3 +199,29 @@ def test_every_entry_point_has_declared_ctypes_types(lib):
     for name in nat.EXPORTED:
         fn = getattr(lib, name)
         assert fn.argtypes is not None and fn.restype is not None, name
+
+
+def test_results_decode_without_gpu(lib):
+    """labs_results_decode is host code: the merit factor of Eq. 3, flip
+    evaluations = steps * N and a signed E, checked on hand-made records."""
+    import numpy as np
+
+    from paper_2504_00987_gb300 import _native as nat
+
+    rec = np.zeros((3, 8), dtype=np.int64)
+    rec[0, 0] = 0x1234
+    rec[0, 4] = (nat.RUN_REACHED << 32) | 100      # E = 100
+    rec[0, 5:8] = (3, 7, 2)                         # generations, steps, trace_len
+    rec[1, 4] = (nat.RUN_BADSTATE << 32) | 0xFFFFFFFF  # E = -1
+    rec[2, 4] = (nat.RUN_BUDGET << 32) | 26         # E = 26
+    rec[2, 6] = 5
+    res = (nat.Result * 3)()
+    assert lib.labs_results_decode(rec.ctypes.data_as(ctypes.c_void_p), 3, 64, 40, res) == nat.LABS_OK
+    assert (res[0].E, res[0].F, res[0].flip_evals, res[0].steps, res[0].generations) == (100, 64 * 64 / 200.0,
+                                                                                         7 * 64, 7, 3)
+    assert res[0].seq[0] == 0x1234 and res[0].instance == 40 and res[0].status == nat.RUN_REACHED
+    assert (res[1].E, res[1].F, res[1].status, res[1].instance) == (-1, 0.0, nat.RUN_BADSTATE, 41)
+    assert res[2].F == 64 * 64 / 52.0 and res[2].flip_evals == 5 * 64
+    assert lib.labs_results_decode(rec.ctypes.data_as(ctypes.c_void_p), 3, 2, 0, res) == nat.LABS_EINVAL
+    assert lib.labs_results_decode(None, 1, 64, 0, res) == nat.LABS_EINVAL
+    assert lib.labs_results_decode(None, 0, 64, 0, None) == nat.LABS_OK

@@ -137,6 +137,9 @@ def check_against_oracle(orc, res, trace, N, K, seed, first, cap, **kw):
         assert g["seq"] == [int(x) for x in o["seq"]]
         assert g["status"] == o["status"] and g["generations"] == o["generations"]
         assert g["steps"] == o["steps"]
+        # decoded by the C boundary (labs_results_decode): Eq. 3 and steps * N
+        assert g["F"] == (N * N / (2.0 * o["E"]) if o["E"] > 0 else 0.0)
+        assert g["flip_evals"] == o["steps"] * N and g["instance"] == first + r
         if trace is not None:
             assert g["trace_len"] == len(otr)
             assert np.array_equal(trace[r, : len(otr)], otr)

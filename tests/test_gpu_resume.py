@@ -85,7 +85,8 @@ def test_records_of_another_run_are_refused(labs):
                            (labs.make_params(N, K, max_generations=4, variant=1), 4, 0),  # other variant
                            (labs.make_params(N - 2, K, max_generations=4), 4, 0)):       # other N, same size
         res = labs.decode_results(labs.mts_resume(P, seed, first, R, state, resume=True), P.N, first)
-        assert all(r["status"] == labs.RUN_BADSTATE and r["generations"] == 0 for r in res)
+        assert all(r["status"] == labs.RUN_BADSTATE and r["generations"] == 0 and r["E"] == -1 and
+                   r["F"] == 0.0 and r["flip_evals"] == 0 for r in res)
         assert np.array_equal(state.cpu().numpy(), before)
     # a fresh start rewrites them
     res = labs.decode_results(labs.mts_resume(labs.make_params(N, K, max_generations=4), 5, 0, R, state,
