@@ -14,16 +14,21 @@
 // LABS_STATIC_MAX_REPLICAS replicas (256 KiB of results plus the flag).
 // Every GPU that loads the library holds this array until the process
 // exits.  Host code only ever sees a host-side stand-in for the array's
-// name, so its device address is looked up with cudaGetSymbolAddress once
-// per device (with that device current) on the first call, and that address
-// is what the kernel receives.  The results are copied straight into the
-// caller's h_out array and widened to labs_result in place, so the host
-// side allocates nothing either.
+// name, so every call looks up the array's device address with
+// cudaGetSymbolAddress, with the caller's device current, and passes that
+// address to the kernel.  The lookup is a host-side table query that
+// allocates nothing; repeating it on every call keeps the address right
+// after a cudaDeviceReset, which reloads the module and may place the array
+// elsewhere (a cached address would then point at freed memory).  The first
+// call on a device, and the first after a reset, loads the library's device
+// code, which is when the array is placed: make that call before any stream
+// capture.  The results are copied straight into the caller's h_out array
+// and widened to labs_result in place, so the host side allocates nothing
+// either.
 #include <cuda_runtime.h>
 
 #include <chrono>
 #include <cstring>
-#include <mutex>
 
 #include "capi_util.h"
 #include "kernels.h"
@@ -35,7 +40,6 @@ constexpr int64_t kMaxReplicas = LABS_STATIC_MAX_REPLICAS;
 constexpr size_t kResultBytes = sizeof(labs_device_result) * static_cast<size_t>(kMaxReplicas);
 constexpr size_t kFlagOffset = kResultBytes;  // a multiple of 256
 constexpr size_t kScratchBytes = kResultBytes + 256;
-constexpr int kMaxDevices = 64;
 
 static_assert(kFlagOffset % 256 == 0, "flag must keep the array's alignment");
 static_assert(sizeof(labs_result) >= sizeof(labs_device_result), "in-place widening needs room");
@@ -43,24 +47,12 @@ static_assert(sizeof(labs_result) >= sizeof(labs_device_result), "in-place widen
 // Shared by every call on a device; keeps the last call's contents.
 static __device__ __align__(256) unsigned char g_mts_static_scratch[kScratchBytes];
 
-std::mutex g_addr_mu;
-void* g_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up once
-// per device, with that device current).
+// Device address of the scratch array on the current device.
 int32_t scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return lcapi::cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return lcapi::fail(LABS_EINVAL, "device %d out of range", dev);
-    std::lock_guard<std::mutex> lk(g_addr_mu);
-    if (g_addr[dev] == nullptr) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_mts_static_scratch);
-        if (e != cudaSuccess) return lcapi::cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_mts_static_scratch);
+    if (e != cudaSuccess) return lcapi::cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    *out = p;
     return LABS_OK;
 }
 
@@ -70,18 +62,11 @@ extern "C" int32_t labs_mts_run_static(const labs_params* P, uint64_t seed, uint
                                        int64_t replicas, labs_result* h_out, labs_stream_t stream) {
     using namespace lcapi;
     const auto t0 = std::chrono::steady_clock::now();
-    if (P == nullptr) return fail(LABS_EINVAL, "params is NULL");
-    LABS_TRY(check_run(P->N, P->K, P->replace_policy, P->target_E, P->max_generations, P->max_steps,
-                       P->max_iter, first_instance, replicas, "params"));
+    lgpu::MtsArgs a;
+    LABS_TRY(make_mts_args(P, seed, first_instance, replicas, &a));
     if (replicas > kMaxReplicas)
         return fail(LABS_EINVAL, "replicas=%lld exceeds the static scratch maximum of %lld",
                     static_cast<long long>(replicas), static_cast<long long>(kMaxReplicas));
-    if (P->trace_cap < 0) return fail(LABS_EINVAL, "trace_cap < 0");
-    LABS_TRY(check_variant(P->variant, P->N, true, "params"));
-    if (P->d_trace != nullptr) LABS_TRY(check_dev(P->d_trace, 16, "d_trace", false));
-    const size_t per_warp = lgpu::mts_smem_per_warp(P->N, P->K);
-    if (per_warp * lgpu::kWarpsPerBlock > 227u * 1024u)
-        return fail(LABS_EINVAL, "population does not fit in shared memory (N=%d, K=%d)", P->N, P->K);
     if (replicas == 0) return ok();
     if (h_out == nullptr) return fail(LABS_EINVAL, "h_out is NULL");
 
@@ -89,26 +74,8 @@ extern "C" int32_t labs_mts_run_static(const labs_params* P, uint64_t seed, uint
     LABS_TRY(scratch_address(&base));
     labs_device_result* d_out = static_cast<labs_device_result*>(base);
     uint32_t* d_flag = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(base) + kFlagOffset);
-
-    lgpu::MtsArgs a;
-    a.N = P->N;
-    a.K = P->K;
-    a.p_comb_u32 = P->p_comb_u32;
-    a.p_mut_u32 = default_p_mut(P->N, P->p_mut_u32, P->variant);
-    a.replace_policy = P->replace_policy;
-    a.target_E = P->target_E;
-    a.max_generations = P->max_generations;
-    a.max_steps = P->max_steps;
-    a.max_iter = P->max_iter;
-    a.variant = P->variant;
-    a.seed = seed;
-    a.first_instance = first_instance;
-    a.replicas = replicas;
     a.d_out = d_out;
     a.d_glf = P->glf ? d_flag : nullptr;
-    a.d_trace = reinterpret_cast<int4*>(P->d_trace);
-    a.trace_cap = P->d_trace ? P->trace_cap : 0;
-    a.smem_per_warp = per_warp;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // The flag keeps the previous call's value: clear it before the launch.

@@ -64,3 +64,49 @@ def test_static_rejects_more_replicas_than_its_scratch(lib):
     rc = lib.labs_mts_run_static(ctypes.byref(P), 0, 0, nat.STATIC_MAX_REPLICAS + 1, res, None)
     assert rc == nat.LABS_EINVAL
     assert b"static scratch maximum" in lib.labs_last_error()
+
+
+def _cudart():
+    for name in ("libcudart.so.13", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so.13"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    pytest.skip("no libcudart to read the default memory pool from")
+
+
+def test_static_allocates_nothing(lib):
+    """The property the entry point exists for: a warmed-up call takes no
+    memory from the device's default pool (where labs_mts_run's
+    cudaMallocAsync scratch comes from) and no device memory at all
+    (cudaMemGetInfo's free bytes do not move).  labs_mts_run on the same
+    arguments is the control: it raises the pool's high-water mark."""
+    from paper_2504_00987_gb300.api import make_params
+
+    rt = _cudart()
+    dev = torch.cuda.current_device()
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
+    used_high = 8  # cudaMemPoolAttrUsedMemHigh
+
+    def reset_high():
+        zero = ctypes.c_uint64(0)
+        assert rt.cudaMemPoolSetAttribute(pool, used_high, ctypes.byref(zero)) == 0
+
+    def high():
+        v = ctypes.c_uint64(0)
+        assert rt.cudaMemPoolGetAttribute(pool, used_high, ctypes.byref(v)) == 0
+        return v.value
+
+    P = make_params(64, 40, max_steps=4_000, glf=True)
+    run(lib, "labs_mts_run_static", P, 1, 0, 256)  # loads the module and places the array
+    torch.cuda.synchronize()
+    reset_high()
+    base = high()
+    free0 = torch.cuda.mem_get_info()[0]
+    run(lib, "labs_mts_run_static", P, 2, 0, 256)
+    torch.cuda.synchronize()
+    assert high() == base
+    assert torch.cuda.mem_get_info()[0] == free0
+    run(lib, "labs_mts_run", P, 2, 0, 256)  # control: this one allocates its scratch
+    assert high() > base
