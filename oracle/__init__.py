@@ -105,7 +105,9 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
+            # LABS_ORACLE_LIB: a library built from a modified copy of labs_oracle.c
+            # (tests/test_oracle_mutants.py plants mistakes that way)
+            L = ctypes.CDLL(os.environ.get("LABS_ORACLE_LIB") or build())
             P = ctypes.POINTER
             u64p, i32p, i64p, u32p = (
                 P(ctypes.c_uint64),

@@ -49,6 +49,59 @@ def test_philox4x64_matches_numpy(orc):
         assert list(raw) == list(a) + list(b)
 
 
+def _weyl(w: int) -> tuple[int, int]:
+    """The Weyl key increments of Philox (SC'11) from their definitions:
+    floor((phi - 1) 2^w) and floor((sqrt(3) - 1) 2^w), in exact integer arithmetic."""
+    import math
+
+    s5 = math.isqrt(5 << (2 * w))    # floor(sqrt(5) 2^w)
+    s3 = math.isqrt(3 << (2 * w))    # floor(sqrt(3) 2^w)
+    return (s5 - (1 << w)) >> 1, s3 - (1 << w)
+
+
+def _philox_naive(w: int, mult: tuple[int, int], ctr, key, rounds: int = 10) -> list[int]:
+    """Philox4xW (Salmon, Moraes, Dror, Shaw, SC'11) with Python integers: each
+    round multiplies counter words 0 and 2 by the two multipliers into
+    double-width products and emits (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2),
+    hi(M0 x0) ^ x3 ^ k1, lo(M0 x0)); the key gains the Weyl increments
+    before every round but the first."""
+    mask = (1 << w) - 1
+    w0, w1 = _weyl(w)
+    x = [int(c) & mask for c in ctr]
+    k0, k1 = int(key[0]) & mask, int(key[1]) & mask
+    for r in range(rounds):
+        if r:
+            k0, k1 = (k0 + w0) & mask, (k1 + w1) & mask
+        p0, p1 = mult[0] * x[0], mult[1] * x[2]
+        x = [(p1 >> w) ^ x[1] ^ k0, p1 & mask, (p0 >> w) ^ x[3] ^ k1, p0 & mask]
+    return x
+
+
+def test_philox4x64_naive_matches_numpy():
+    """The naive round structure and key schedule, on 64-bit words, equal numpy.random.Philox."""
+    mult64 = (0xD2E7470EE14C6C93, 0xCA5A826395121157)
+    rng = np.random.default_rng(7)
+    for _ in range(10):
+        key = rng.integers(0, 2**63, size=2, dtype=np.int64).astype(np.uint64)
+        ctr0 = int(rng.integers(0, 2**62))
+        raw = np.random.Philox(key=key, counter=np.array([ctr0, 0, 0, 0], dtype=np.uint64)).random_raw(4)
+        assert list(map(int, raw)) == _philox_naive(64, mult64, [ctr0 + 1, 0, 0, 0], key)
+
+
+def test_philox4x32_matches_naive_definition(orc):
+    """The oracle's Philox4x32-10 equals the naive big-integer one (same
+    structure as the numpy-checked 64-bit form, Weyl increments derived from
+    phi and sqrt 3, the 32-bit multipliers of SC'11) on 10^4 random counters
+    and keys, so a wrong digit in any of its constants fails here."""
+    mult32 = (0xD2511F53, 0xCD9E8D57)
+    rng = np.random.default_rng(11)
+    ctr = rng.integers(0, 1 << 32, size=(10_000, 4), dtype=np.uint64)
+    keys = rng.integers(0, 1 << 32, size=(10_000, 2), dtype=np.uint64)
+    for i in range(10_000):
+        c, k = [int(v) for v in ctr[i]], [int(v) for v in keys[i]]
+        assert list(map(int, orc.philox4x32_10(c, k))) == _philox_naive(32, mult32, c, k), i
+
+
 def test_philox_batch_equals_single_calls(orc):
     """The batched oracle generator is the single-counter one at every row."""
     rng = np.random.default_rng(3)
@@ -337,6 +390,7 @@ def replay_mts(orc, P, seed, inst, res, genlog):
         pop.append(member)
     popE = [np_energy(s)[0] for s in pop]
     bestE = min(popE)
+    best = pop[popE.index(bestE)]  # lowest index among the minima
     for L in genlog:
         g = L.g
         pre_mut = orc.words_to_spins(list(L.pre_mut)[:W], N)
@@ -368,7 +422,8 @@ def replay_mts(orc, P, seed, inst, res, genlog):
             assert child[0] == 1 and pre_tabu[0] == 1
         if skew:
             assert is_skew(child) and is_skew(pre_tabu)
-        bestE = min(bestE, L.E_child)
+        if L.E_child < bestE:  # Alg. 1: bestSeq changes only on a strictly lower energy
+            bestE, best = L.E_child, child
         if P.replace_policy == 0:
             slot = ri(0, K - 1, draw(g, 2, 2, 0))
         else:
@@ -376,6 +431,7 @@ def replay_mts(orc, P, seed, inst, res, genlog):
         assert L.replace == slot
         pop[slot], popE[slot] = child, L.E_child
     assert res["E"] == bestE == np_energy(orc.words_to_spins(res["seq"], N))[0]
+    assert np.array_equal(orc.words_to_spins(res["seq"], N), best)
     assert res["generations"] == len(genlog)
     assert res["steps"] == sum(L.steps for L in genlog)
 
