@@ -265,6 +265,7 @@ def run_gpu(args) -> None:
     total_ms, e2e_step_ms = parallel.max_over_ranks(pg, [local_ms, sum(e2e_ms) / len(e2e_ms)], dev)
     lbest = min(res, key=lambda r: (r["E"], r["instance"]))
     best_E, best_inst = parallel.best_over_ranks(pg, lbest["E"], lbest["instance"], dev)
+    extras = None if args.no_extras else c2_extras(args, torch, labs, pg, dev, world, rank, stream)
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
@@ -304,12 +305,48 @@ def run_gpu(args) -> None:
         "wall_s_timed": wall,
         "clocks": clock,
     }
+    if extras is not None:
+        line.update(extras)
     if world == 1 and not args.no_cpu_baseline:
         cores = cpu_cores()
         line["cpu_baseline"] = cpu_baseline_run(2 * cores, cores, STEPS_PER_REPLICA)
+        if extras is not None:
+            line["sweep_cpu_baseline"] = sweep_cpu_baseline(cores)
     print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()
+
+
+def c2_extras(args, torch, labs, pg, dev, world, rank, stream) -> dict:
+    """The N = 92..120 configuration beside the headline: its throughput sweep
+    (16 replicas per SM x 10^6 tabu steps per N, one timed launch each) and its
+    time to target (the oracle's one-minute best energy per N, the launch's
+    replicas stopped by the global termination flag; p50/p99 over --tts-runs
+    seeds per N)."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    reps, steps = sms * 16, 1_000_000
+    first, _ = parallel.shard(world, rank, reps)
+    rows = sweep_rows(torch, labs, pg, dev, first, reps, steps, 1, 1, stream, world)
+    targets = load_targets("sweep_n92_120")
+    treps, cap = sms * 8, 10_000_000
+    trows = tts_rows(torch, labs, SWEEP_NS, targets, treps, cap, args.tts_runs, stream, pg=pg, rank=rank)
+    return {
+        "sweep_n92_120": {"workload": f"N=92..120 step 4, K=100, {reps} replicas x {steps} tabu steps per N "
+                                      f"per GPU, one timed launch per N",
+                          "flip_evals_per_s": {str(r["N"]): r["flip_evals_per_s"] for r in rows},
+                          "best_E": {str(r["N"]): r["best_E"] for r in rows},
+                          "value": sum(r["flips"] for r in rows) / (sum(r["ms"] for r in rows) / 1e3)},
+        "tts_n92_120": {"workload": f"{treps} replicas per GPU with the global termination flag, K=100, cap "
+                                    f"{cap} steps per replica, seeds 1000..{999 + args.tts_runs}"
+                                    + (", ranks stop together between slices of 100 generations"
+                                       if world > 1 else ""),
+                        "targets": "tests/golden/targets.json sweep_n92_120 (the oracle's one-minute best)",
+                        "runs_per_N": args.tts_runs,
+                        "reached": {str(r["N"]): r["reached"] for r in trows},
+                        "target_E": {str(r["N"]): r["target_E"] for r in trows}},
+        "tts_p50_s": {str(r["N"]): r["p50_s"] for r in trows},
+        "tts_p99_s": {str(r["N"]): r["p99_s"] for r in trows},
+    }
 
 
 # ---------------------------------------------------------------- other workloads
@@ -354,9 +391,46 @@ def timed_launch(torch, fn, stream):
     return s.elapsed_time(e), out
 
 
+SWEEP_NS = list(range(92, 121, 4))
+
+
+def sweep_rows(torch, labs, pg, dev, first, reps, steps, timed, warmup, stream, world):
+    """C2 throughput: per N = 92..120 step 4, `timed` launches of `reps` replicas x
+    `steps` tabu steps (K=100) after `warmup` short ones; time = max over ranks."""
+    rows = []
+    for n in SWEEP_NS:
+        P = labs.make_params(n, 100, max_steps=steps)
+        warm = labs.make_params(n, 100, max_steps=max(1, steps // 100))
+        for _ in range(warmup):
+            labs.mts_launch(warm, 0, first, reps)
+        ms_list = []
+        for _ in range(timed):
+            ms, out = timed_launch(torch, lambda: labs.mts_launch(P, 0, first, reps, stream=stream), stream)
+            ms_list.append(ms)
+        ms = parallel.max_over_ranks(pg, [statistics.mean(ms_list)], dev)[0]
+        res = labs.decode_results(out, n, first)
+        assert sum(r["steps"] for r in res) == reps * steps, "every replica must use its full step budget"
+        lb = min(res, key=lambda r: (r["E"], r["instance"]))
+        bE, bi = parallel.best_over_ranks(pg, lb["E"], lb["instance"], dev)
+        flips = reps * steps * n * world
+        rows.append({"N": n, "ms": ms, "flips": flips, "flip_evals_per_s": flips / (ms / 1e3),
+                     "pair_terms_per_s": flips * (n - 1) / (ms / 1e3), "best_E": bE,
+                     "best_merit_factor": n * n / (2.0 * bE), "best_instance": bi})
+    return rows
+
+
+def sweep_cpu_baseline(cores: int, steps: int = 10_000) -> dict:
+    """The oracle on the sweep's N and parameters: one replica per host core."""
+    per_n = {str(n): cpu_baseline_run(cores, cores, steps, n)["value"] for n in SWEEP_NS}
+    return {"value": statistics.mean(per_n.values()), "unit": "flip-evals/s", "cores": cores,
+            "kind": "oracle", "per_N": per_n,
+            "sample": f"per N: {cores} replicas (instances 0..{cores - 1}) x {steps} tabu steps, "
+                      f"one replica per thread; value = mean over N"}
+
+
 def run_sweep(args) -> None:
     """N = 92, 96, ..., 120 (two words), one K=100 population per warp, 16 warps per SM
-    (4 % more flip-evals/s than 8 on GB300: more warps hide the step's latencies)."""
+    (more warps hide the step's latencies)."""
     torch, dev, pg, world, rank = gpu_context(args)
     import paper_2504_00987_gb300 as labs
 
@@ -365,37 +439,9 @@ def run_sweep(args) -> None:
     steps = args.steps_per_replica or 1_000_000
     first, _ = parallel.shard(world, rank, reps)
     stream = torch.cuda.current_stream()
-    rows, tot_flips, tot_ms = [], 0, 0.0
-    for n in range(92, 121, 4):
-        P = labs.make_params(n, 100, max_steps=steps)
-        warm = labs.make_params(n, 100, max_steps=max(1, steps // 100))
-        for _ in range(args.warmup):
-            labs.mts_launch(warm, 0, first, reps)
-        ms_list = []
-        for _ in range(args.steps):
-            ms, out = timed_launch(torch, lambda: labs.mts_launch(P, 0, first, reps, stream=stream), stream)
-            ms_list.append(ms)
-        ms = parallel.max_over_ranks(pg, [statistics.mean(ms_list)], dev)[0]
-        res = labs.decode_results(out, n, first)
-        lb = min(res, key=lambda r: (r["E"], r["instance"]))
-        bE, bi = parallel.best_over_ranks(pg, lb["E"], lb["instance"], dev)
-        flips = reps * steps * n * world
-        rows.append({"N": n, "ms": ms, "flip_evals_per_s": flips / (ms / 1e3),
-                     "pair_terms_per_s": flips * (n - 1) / (ms / 1e3), "best_E": bE,
-                     "best_merit_factor": n * n / (2.0 * bE), "best_instance": bi})
-        tot_flips += flips
-        tot_ms += ms
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        # the oracle on the same N and parameters: one replica per host core, 10^4 steps each
-        cores = cpu_cores()
-        per_n = {}
-        for n in range(92, 121, 4):
-            per_n[str(n)] = cpu_baseline_run(cores, cores, 10_000, n)["value"]
-        cpu = {"value": statistics.mean(per_n.values()), "unit": "flip-evals/s", "cores": cores,
-               "kind": "oracle", "per_N": per_n,
-               "sample": f"per N: {cores} replicas (instances 0..{cores - 1}) x 10000 tabu steps, "
-                         f"one replica per thread; value = mean over N"}
+    rows = sweep_rows(torch, labs, pg, dev, first, reps, steps, args.steps, args.warmup, stream, world)
+    tot_flips, tot_ms = sum(r.pop("flips") for r in rows), sum(r["ms"] for r in rows)
+    cpu = sweep_cpu_baseline(cpu_cores()) if world == 1 and not args.no_cpu_baseline else None
     if rank == 0:
         print(json.dumps({
             "cpu_baseline": cpu,
@@ -429,11 +475,63 @@ def fit_exponential(Ns, medians):
             "N_min_fit": int(min(Ns)), "N_max_fit": int(max(Ns))}
 
 
-def tts_rows(torch, labs, Ns, targets, reps, cap, runs, stream, variant=0, replace_policy=0):
+def tts_run_ranks(torch, labs, pg, dev, n, target, seed, first, reps, cap, state, out, flag, stream,
+                  slice_gens=100):
+    """One time-to-target run on every rank: the rank's replicas advance in slices
+    of `slice_gens` generations (labs_mts_resume), and after each slice the ranks
+    OR their reached flags (parallel.run_until_any), so every GPU stops after the
+    slice in which any replica of the job reached the target.  Returns (seconds,
+    reached, tabu steps of this rank's replicas)."""
+    gens = [0]
+
+    def run_slice(i):
+        gens[0] += slice_gens
+        P = labs.make_params(n, 100, max_generations=gens[0], max_steps=cap, target_E=target, glf=True)
+        labs.mts_resume(P, seed, first, reps, state, resume=i > 0, out=out, glf_flag=flag, stream=stream)
+        return bool(((out[:, 4] >> 32) == labs.RUN_REACHED).any().item())
+
+    flag.zero_()
+    pg.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    max_slices = cap // (slice_gens * max(1, n // 2)) + 1  # a generation takes at least N/2 steps
+    _, ok = parallel.run_until_any(pg, run_slice, max_slices, dev)
+    torch.cuda.synchronize()
+    dt = parallel.max_over_ranks(pg, [time.perf_counter() - t0], dev)[0]
+    return dt, ok, int(out[:, 6].sum().item())
+
+
+def tts_rows(torch, labs, Ns, targets, reps, cap, runs, stream, variant=0, replace_policy=0, pg=None,
+             rank=0):
     """Per N: `runs` launches of `reps` replicas (seeds 1000, 1001, ...) that stop,
-    all of them, as soon as one reaches targets[N]; seconds to target per run."""
+    all of them, as soon as one reaches targets[N]; seconds to target per run.
+    Under torchrun (pg given) each rank runs its own `reps` replicas and the
+    ranks share the stop flag between slices of generations (tts_run_ranks)."""
     import numpy as np
 
+    if pg is not None:
+        if variant or replace_policy:
+            raise ValueError("variants run on one GPU")
+        dev = stream.device
+        rows = []
+        for n in Ns:
+            state = torch.empty(reps * labs.mts_state_bytes(n, 100), dtype=torch.uint8, device=dev)
+            out = torch.empty((reps, 8), dtype=torch.int64, device=dev)
+            flag = torch.zeros(1, dtype=torch.int32, device=dev)
+            times, work, reached = [], [], 0
+            for run in range(runs):
+                dt, ok, st = tts_run_ranks(torch, labs, pg, dev, n, targets[n], 1000 + run, rank * reps, reps,
+                                           cap, state, out, flag, stream)
+                st = parallel.sum_over_ranks(pg, [float(st)], dev)[0]
+                reached += ok
+                times.append(dt if ok else float("inf"))
+                work.append(st if ok else float("inf"))
+            t, w = np.array(times), np.array(work)
+            rows.append({"N": n, "target_E": targets[n], "runs": runs, "reached": reached,
+                         "p50_s": float(np.percentile(t, 50)), "p99_s": float(np.percentile(t, 99)),
+                         "q1_s": float(np.percentile(t, 25)), "q3_s": float(np.percentile(t, 75)),
+                         "p50_steps": float(np.percentile(w, 50)), "times_s": [round(x, 6) for x in times]})
+        return rows
     rows = []
     for n in Ns:
         target = targets[n]
@@ -486,7 +584,7 @@ def run_tts(args) -> None:
     cap = args.steps_per_replica or 10_000_000
     stream = torch.cuda.current_stream()
     Ns = [int(x) for x in args.tts_n.split(",")] if args.tts_n else sorted(targets)
-    rows = tts_rows(torch, labs, Ns, targets, reps, cap, args.runs, stream)
+    rows = tts_rows(torch, labs, Ns, targets, reps, cap, args.runs, stream, pg=pg, rank=rank)
     for r in rows:
         r.pop("times_s")
     if rank == 0:
@@ -609,73 +707,6 @@ def run_skew_ab(args) -> None:
             "fit_restricted_p50_steps": median_fit(rows_s, "p50_steps"),
             "fit_unrestricted_p50_s": median_fit(rows_u), "fit_restricted_p50_s": median_fit(rows_s),
             "per_N": per_n}), flush=True)
-
-
-def table2_energy(n: int) -> int:
-    """The lowest energy Table II prints for N (tests/golden/table2_new_records.txt)."""
-    best = None
-    with open(os.path.join(ROOT, "tests", "golden", "table2_new_records.txt")) as f:
-        for line in f:
-            parts = line.split()
-            if parts and not line.startswith("#") and int(parts[0]) == n:
-                best = int(parts[1]) if best is None else min(best, int(parts[1]))
-    if best is None:
-        raise SystemExit(f"Table II has no entry for N={n}")
-    return best
-
-
-def run_record(args) -> None:
-    """A record search as the paper runs them (Sec. IV), bounded in time: 16
-    replicas per SM with the global termination flag race to Table II's energy
-    for N, in slices of generations continued with labs_mts_resume (so a search
-    can be stopped and resumed at any slice).  Populations stagnate after some
-    seconds, so every --record-epoch-s the search restarts with fresh replicas
-    (the next block of instance numbers).  Reports the best E over time and the
-    time to the target if it is reached within --record-seconds."""
-    torch, dev, pg, world, rank = gpu_context(args)
-    import paper_2504_00987_gb300 as labs
-
-    n = args.record_n
-    target = table2_energy(n)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    reps = args.replicas or sms * 16
-    K, seed = 100, args.record_seed
-    state = torch.empty(reps * labs.mts_state_bytes(n, K), dtype=torch.uint8, device=dev)
-    flag = torch.zeros(1, dtype=torch.int32, device=dev)
-    out = torch.empty((reps, 8), dtype=torch.int64, device=dev)
-    gens, history, reached_s, best, steps, epoch = 500, [], None, None, 0, 0
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    while time.perf_counter() - t0 < args.record_seconds and reached_s is None:
-        first, G, t_epoch = epoch * reps, 0, time.perf_counter()
-        while (time.perf_counter() - t_epoch < args.record_epoch_s
-               and time.perf_counter() - t0 < args.record_seconds):
-            G += gens
-            P = labs.make_params(n, K, max_generations=G, target_E=target, glf=True)
-            labs.mts_resume(P, seed, first, reps, state, resume=G > gens, out=out, glf_flag=flag)
-            res = labs.decode_results(out, n, first)
-            elapsed = time.perf_counter() - t0
-            b = min(res, key=lambda r: (r["E"], r["instance"]))
-            if best is None or b["E"] < best["E"]:
-                best = b
-                history.append({"s": round(elapsed, 3), "E": b["E"], "epoch": epoch, "generations": G})
-            if any(r["status"] == labs.RUN_REACHED for r in res):
-                reached_s = elapsed
-                break
-        steps += sum(r["steps"] for r in res)
-        epoch += 1
-    if rank == 0:
-        print(json.dumps({
-            "metric": "best E within the time budget", "value": best["E"], "unit": "E", "n_gpus": world,
-            "higher_is_better": False, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"record_n{n}: {reps} replicas, K={K}, seed {seed}, target = Table II E "
-                                   f"{target}, slices of {gens} generations, fresh replicas every "
-                                   f"{args.record_epoch_s} s, budget {args.record_seconds} s"},
-            "epochs": epoch,
-            "target_E": target, "reached": reached_s is not None, "time_to_target_s": reached_s,
-            "best_merit_factor": n * n / (2.0 * best["E"]), "best_instance": best["instance"],
-            "best_seq_words": best["seq"], "tabu_steps": steps, "flip_evals_per_s": steps * n / (time.perf_counter() - t0),
-            "history": history}), flush=True)
 
 
 def run_batch(args) -> None:
@@ -862,11 +893,14 @@ def main() -> None:
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line without its N=92..120 sweep and time-to-target keys")
+    ap.add_argument("--tts-runs", type=int, default=50, help="default line: time-to-target runs per N")
     ap.add_argument("--replicas", type=int, default=0, help="profiling only: override replicas")
     ap.add_argument("--steps-per-replica", type=int, default=0, help="profiling only: override budget")
     ap.add_argument("--n", type=int, default=0, help="profiling only: override N of the default workload")
     ap.add_argument("--workload", choices=["replicas_n64", "sweep_n92_120", "tts", "tts_ab", "skew_ab", "batch",
-                                           "serve", "skew", "record"],
+                                           "serve", "skew"],
                     default="replicas_n64")
     ap.add_argument("--runs", type=int, default=50, help="tts: runs per N")
     ap.add_argument("--tts-n", default="", help="tts: comma-separated N (default: all; tts_ab: first five)")
@@ -874,10 +908,6 @@ def main() -> None:
                     help="tts: oracle one-minute best (N=92..120) or exact optimum (N=16..36)")
     ap.add_argument("--fit-min-n", type=int, default=30,
                     help="tts: smallest N of the second steps fit (above the one-generation floor)")
-    ap.add_argument("--record-n", type=int, default=92, help="record: N (a Table II length)")
-    ap.add_argument("--record-seconds", type=float, default=120.0, help="record: time budget")
-    ap.add_argument("--record-epoch-s", type=float, default=10.0, help="record: seconds before fresh replicas")
-    ap.add_argument("--record-seed", type=int, default=2025, help="record: Philox seed")
     ap.add_argument("--requests", type=int, default=20_000, help="serve: requests")
     ap.add_argument("--baseline-requests", type=int, default=400, help="serve: plain-form prefix")
     ap.add_argument("--slots", type=int, default=0, help="serve: resident slots")
@@ -897,8 +927,6 @@ def main() -> None:
         run_tts_ab(args)
     elif args.workload == "skew_ab":
         run_skew_ab(args)
-    elif args.workload == "record":
-        run_record(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "serve":

@@ -50,11 +50,3 @@ def test_clock_summary_from_samples(bench, tmp_path):
     out = s.summary()
     assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
     assert out["reasons"] == ["sw_power_cap"]  # the other GPU's slowdown is not ours
-
-
-def test_table2_energy_lookup(bench):
-    """The record search's target is Table II's lowest energy for the length."""
-    assert bench.table2_energy(92) == 490 and bench.table2_energy(98) == 529
-    assert bench.table2_energy(120) == 824
-    with pytest.raises(SystemExit):
-        bench.table2_energy(93)
