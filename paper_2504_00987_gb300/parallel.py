@@ -63,3 +63,24 @@ def best_over_ranks(dist, E: int, instance: int, device=None) -> tuple[int, int]
     dist.all_reduce(key, op=dist.ReduceOp.MIN)
     k = int(key.item())
     return k >> 32, k & 0xFFFFFFFF
+
+
+def any_over_ranks(dist, flag: bool, device=None) -> bool:
+    """True on every rank if `flag` is true on any rank (identity for one process)."""
+    return max_over_ranks(dist, [1.0 if flag else 0.0], device)[0] > 0.0
+
+
+def run_until_any(dist, run_slice, max_slices: int, device=None) -> tuple[int, bool]:
+    """The global termination flag of Alg. 3 across GPUs.  Within one GPU the
+    replicas of a launch share a device flag; across ranks every rank runs its
+    replicas in slices (`run_slice(i)` runs slice i, e.g. the next generations
+    of resumable replicas, and returns True if one of this rank's replicas
+    reached the target), and after every slice the ranks take the OR of their
+    flags, so all of them stop after the same slice once any has reached.
+    Returns (slices run, reached on some rank)."""
+    if max_slices < 0:
+        raise ValueError("max_slices < 0")
+    for i in range(max_slices):
+        if any_over_ranks(dist, bool(run_slice(i)), device):
+            return i + 1, True
+    return max_slices, False
