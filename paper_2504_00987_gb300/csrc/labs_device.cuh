@@ -101,6 +101,36 @@ __device__ __forceinline__ void shr_uniform(const uint32_t (&in)[NW], int s, uin
     for (int w = 0; w < NW; ++w) out[w] = __funnelshift_r(a[w], w + 1 < NW ? a[w + 1] : 0u, bs);
 }
 
+// oa = a >> s and ob = b >> s for two NW-word vectors and one warp-uniform
+// shift 0 <= s < 32*NW: one select network and one set of funnel shifts
+// shared by both.
+template <int NW>
+__device__ __forceinline__ void shr_uniform2(const uint32_t (&a)[NW], const uint32_t (&b)[NW], int s,
+                                             uint32_t (&oa)[NW], uint32_t (&ob)[NW]) {
+    uint32_t x[NW], y[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        x[w] = a[w];
+        y[w] = b[w];
+    }
+    const int ws = s >> 5;
+#pragma unroll
+    for (int step = 1; step < NW; step <<= 1) {
+        const bool take = (ws & step) != 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            x[w] = take ? (w + step < NW ? x[w + step] : 0u) : x[w];
+            y[w] = take ? (w + step < NW ? y[w + step] : 0u) : y[w];
+        }
+    }
+    const int bs = s & 31;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        oa[w] = __funnelshift_r(x[w], w + 1 < NW ? x[w + 1] : 0u, bs);
+        ob[w] = __funnelshift_r(y[w], w + 1 < NW ? y[w + 1] : 0u, bs);
+    }
+}
+
 // Flip bit i (warp-uniform) of an NW-word vector.
 template <int NW>
 __device__ __forceinline__ void flip_bit(uint32_t (&v)[NW], int i) {

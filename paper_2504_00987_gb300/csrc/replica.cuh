@@ -154,6 +154,7 @@ __device__ void replica_init(const ReplicaCfg& a, uint32_t* __restrict__ pop,
 template <int NW>
 __device__ __forceinline__ bool replica_should_stop(const ReplicaCfg& a, ReplicaState<NW>& st,
                                                     const uint32_t* glf) {
+    if (st.status == LABS_RUN_SYNC_LOST) return true;
     if (a.target_E >= 0 && st.E_best <= a.target_E) {
         st.status = LABS_RUN_REACHED;
         return true;
@@ -171,12 +172,18 @@ __device__ __forceinline__ bool replica_should_stop(const ReplicaCfg& a, Replica
 }
 
 // One generation g = st.g.  Returns the tabu steps it took.
-template <int NW, bool TRACE = false, bool SKEW = false>
+// WPS = 2: this warp is half HALF of a replica on two warps (tabu_search);
+// it holds its own copy of the population and takes the same decisions as
+// its partner, with which it meets through `link` inside the tabu search.
+// The global termination flag is not supported there (glf must be null: the
+// two warps could read it at different times).
+template <int NW, bool TRACE = false, bool SKEW = false, int WPS = 1, int HALF = 0>
 __device__ int64_t replica_generation(const ReplicaCfg& a, ReplicaState<NW>& st,
                                       uint32_t* __restrict__ pop, int32_t* __restrict__ popE,
                                       int32_t* __restrict__ Cs, int4* __restrict__ trace,
                                       int64_t trace_cap, int64_t& trace_len, uint32_t* glf,
-                                      int lane) {
+                                      int lane, PairLink* link = nullptr, uint32_t* xseq = nullptr) {
+    static_assert(WPS == 1 || (!SKEW && !TRACE), "two warps per replica: unrestricted, untraced");
     const int N = a.N, K = a.K;
     const uint32_t gg = static_cast<uint32_t>(st.g);
     const uint32_t p_mut = a.p_mut_u32;
@@ -231,10 +238,14 @@ __device__ int64_t replica_generation(const ReplicaCfg& a, ReplicaState<NW>& st,
                                                       trace, trace_cap, trace_len, lane);
     } else {
         to = (a.variant & LABS_VARIANT_FIX_FIRST_SPIN)
-                 ? tabu_search<NW, TRACE, true>(child, N, a.key, a.inst, gg, max_iter, budget, Cs, trace,
-                                                trace_cap, trace_len, lane)
-                 : tabu_search<NW, TRACE, false>(child, N, a.key, a.inst, gg, max_iter, budget, Cs, trace,
-                                                 trace_cap, trace_len, lane);
+                 ? tabu_search<NW, TRACE, true, WPS, HALF>(child, N, a.key, a.inst, gg, max_iter, budget, Cs,
+                                                           trace, trace_cap, trace_len, lane, link, xseq)
+                 : tabu_search<NW, TRACE, false, WPS, HALF>(child, N, a.key, a.inst, gg, max_iter, budget, Cs,
+                                                            trace, trace_cap, trace_len, lane, link, xseq);
+    }
+    if (to.fault) {  // the pair lost step: stop the replica, report it
+        st.status = LABS_RUN_SYNC_LOST;
+        return to.steps;
     }
     st.steps += to.steps;
     if (to.E_best < st.E_best) {
@@ -291,17 +302,20 @@ __device__ __forceinline__ void replica_store_result(const ReplicaState<NW>& st,
     }
 }
 
-// A whole replica from scratch to its stop condition.
-template <int NW, bool TRACE = false, bool SKEW = false>
+// A whole replica from scratch to its stop condition.  WPS = 2: both warps
+// run it (see replica_generation); the lower half stores the result.
+template <int NW, bool TRACE = false, bool SKEW = false, int WPS = 1, int HALF = 0>
 __device__ __forceinline__ void replica_run(const ReplicaCfg& a, uint32_t* pop, int32_t* popE,
                                             int32_t* Cs, int4* trace, int64_t trace_cap,
-                                            uint32_t* glf, labs_device_result* out, int lane) {
+                                            uint32_t* glf, labs_device_result* out, int lane,
+                                            PairLink* link = nullptr, uint32_t* xseq = nullptr) {
     ReplicaState<NW> st;
     int64_t trace_len = 0;
     replica_init<NW, SKEW>(a, pop, popE, st, lane);
     while (!replica_should_stop<NW>(a, st, glf))
-        replica_generation<NW, TRACE, SKEW>(a, st, pop, popE, Cs, trace, trace_cap, trace_len, glf, lane);
-    replica_store_result<NW>(st, trace_len, out, lane);
+        replica_generation<NW, TRACE, SKEW, WPS, HALF>(a, st, pop, popE, Cs, trace, trace_cap, trace_len, glf,
+                                                       lane, link, xseq);
+    if (HALF == 0) replica_store_result<NW>(st, trace_len, out, lane);
 }
 
 }  // namespace lgpu

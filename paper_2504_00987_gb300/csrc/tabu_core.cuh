@@ -82,9 +82,49 @@ __device__ __forceinline__ int32_t thread_energy(const uint32_t (&B)[NW], int N)
 }
 
 struct TabuOut {
-    int64_t steps;
-    int32_t E_best;
+    int64_t steps = 0;
+    int32_t E_best = 0;
+    bool fault = false;  // the two warps of a replica lost step (a bounded wait ran out)
 };
+
+// Two warps of one CTA sharing one replica ("warps per sequence" = 2): each
+// runs the whole replica on its own copy of the state and scores half of
+// the neighbours; per step they exchange their admissible minima through
+// this shared-memory word pair.  Exchange x of a pair uses slot [x & 1] (so
+// a warp that runs ahead never overwrites a word its partner has not read:
+// it cannot publish x + 2 before the partner published x + 1, which comes
+// after the partner read x); a word holds (x mod 2^24) << 40 | value.
+struct PairLink {
+    unsigned long long slot[2][2];  // [x & 1][half]
+};
+
+constexpr uint32_t kPairSpinLimit = 1u << 22;  // ~10^8 cycles, far beyond one step's skew
+
+// Publishes this warp's value v (< 2^40) of exchange x and returns the
+// partner's in `other`.  Lane 0 spins on the partner's word with a bounded
+// number of polls; false if they run out (the caller stops the replica).
+__device__ __forceinline__ bool pair_exchange(PairLink* link, int half, uint32_t x, uint64_t v,
+                                              uint64_t& other, int lane) {
+    const uint64_t tag = static_cast<uint64_t>(x & 0xFFFFFFu) << 40;
+    bool ok = true;
+    uint64_t w = 0;
+    if (lane == 0) {
+        volatile unsigned long long* mine = &link->slot[x & 1u][half];
+        volatile unsigned long long* theirs = &link->slot[x & 1u][half ^ 1];
+        *mine = tag | v;
+        for (uint32_t it = 0;; ++it) {
+            w = *theirs;
+            if ((w >> 40) == (x & 0xFFFFFFu)) break;
+            if (it >= kPairSpinLimit) {
+                ok = false;
+                break;
+            }
+        }
+    }
+    ok = __shfl_sync(kFull, ok ? 1 : 0, 0) != 0;
+    other = __shfl_sync(kFull, static_cast<unsigned long long>(w), 0) & ((1ull << 40) - 1);
+    return ok;
+}
 
 // Bit-plane count bound: |C_k| <= N - 1 < 32*NW, so C_k fits in
 // bitlen(32*NW - 1) + 1 two's-complement bits.
@@ -265,26 +305,40 @@ __device__ __forceinline__ void pivot_windows(const uint32_t (&B)[NW], const uin
 // the energy after flipping j is E_j = E + 4(N-1) + 8 M_j - 4 s_j R_j (the
 // delta_k(j)(2 C_k + delta_k(j)) sum of Table I, expanded).  R_j is set up
 // once per search on the bit planes of C_k; after the move p (s_p before
-// it, C and C' the correlations before and after, d = |p - j|) it changes
-// exactly by
-//   R'_j = R_j - 2 s_p (C_d + C'_d + F_j) - 2 s_j          (j != p)
+// it, C and C' the correlations before and after, d = |p - j|, s'_j after
+// the move) it changes exactly by
+//   R'_j = R_j - 2 s_p (C_d + C'_d + F_j) - 2 s'_j          (j != p)
 //   R'_p = R_p - 2 s_p (N - 1 + 2 M_p)
 // with F_j = sum_{k>=1} s~_{p+k} s~'_{j-k} + sum_{k>=1} s~_{p-k} s~'_{j+k}
 // (s~' after the move).  Derivation: R'_j - R_j = sum_k C_k (s~'-s~)
 // (terms j+-k = p: -2 s_p C_d) + sum_k delta_k(p) (s~'_{j+k} + s~'_{j-k});
 // the second sum pairs the windows of p and j: its same-direction pairs
 // (p+k, j+k), (p-k, j-k) cover every product of C'_d except s'_p s'_j, and
-// its crossed pairs are F_j.  F_j is two masked popcounts over the windows
-// of p and j (the crossed pairs agree or disagree), C_d and C'_d are read
-// from the two shared buffers, so a step costs about one bit plane of the
-// from-scratch scoring instead of one per bit of max |C_k|.
-template <int NW, bool TRACE, bool FIX_FIRST = false>
+// its crossed pairs are F_j.  At j = p the crossed pairs give F_p = 2 M_p and
+// s'_p = -s_p, so the first line gives the second when C_0 + C'_0 = N: the
+// two buffers hold ceil(N/2) and floor(N/2) at k = 0 and one update serves
+// every j.  F_j is two masked popcounts over the windows of p and j (the
+// crossed pairs agree or disagree), C_d and C'_d are read from the two
+// shared buffers, so a step costs about one bit plane of the from-scratch
+// scoring instead of one per bit of max |C_k|.
+//
+// WPS = 2 (two warps per replica, HALF = which one): the warp scores and
+// updates only the neighbours j = lane + 32q of its half of q, keeps its own
+// copy of everything else (pivot, correlations, bestSeqTS), and the two
+// minima meet through `link`; the lower half's neighbours come first in
+// ascending j for the tie pick.  Both warps take every decision from the
+// same values, so they run the same steps; `xseq` counts the pair's
+// exchanges.  A bounded wait that runs out ends the search with fault set.
+template <int NW, bool TRACE, bool FIX_FIRST = false, int WPS = 1, int HALF = 0>
 __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key,
                                const uint32_t inst, const uint32_t g, const int max_iter,
                                const int64_t budget, int32_t* __restrict__ Cs,
                                int4* __restrict__ trace, const int64_t trace_cap,
-                               int64_t& trace_len, const int lane) {
+                               int64_t& trace_len, const int lane, PairLink* link = nullptr,
+                               uint32_t* xseq = nullptr) {
+    static_assert(WPS == 1 || (WPS == 2 && NW % 2 == 0 && HALF >= 0 && HALF < 2), "warps per sequence");
     constexpr int NB = 32 * NW;
+    constexpr int QB = HALF * (NW / WPS), QE = (HALF + 1) * (NW / WPS);  // this warp's q
     // Correlations after a move are recomputed from the pivot's windows when
     // they are short (fewer ALU-pipe instructions than the per-k update) and
     // updated per k otherwise.
@@ -316,12 +370,13 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
     uint32_t mmask[NW][NW], mX[NW];
     uint32_t jvalid = 0;  // bit q: j < N and j may move
 #pragma unroll
-    for (int q = 0; q < NW; ++q) {
+    for (int q = 0; q < NW; ++q) mX[q] = word_lowmask(q, N - lane);
+#pragma unroll
+    for (int q = QB; q < QE; ++q) {
         tabu[q] = 0;
         const int j = lane + 32 * q;
         Lq[q] = min(j, N - 1 - j);
         jvalid |= (j < N && !(FIX_FIRST && j == 0) ? 1u : 0u) << q;
-        mX[q] = word_lowmask(q, N - lane);
 #pragma unroll
         for (int w = 0; w <= q && w + q < NW; ++w)
             mmask[q][w] = word_lowmask(w, Lq[q] + 1) & (w == 0 ? ~1u : kFull);
@@ -350,13 +405,21 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
         prefix_own<NW>(c, lane, pc);
         mirror_terms<NW>(pc, N, lane, Cs, T);
 #pragma unroll
-        for (int q = 0; q < NW; ++q) R[q] = 2 * S[q] - T[q];
+        for (int q = QB; q < QE; ++q) R[q] = 2 * S[q] - T[q];
     }
-    int32_t* Ccur = Cs;       // C_k of the pivot, k = 0 .. NB-1 (C_0 = 0)
-    int32_t* Cnxt = Cs + NB;  // C_k after the move
+    // C_k of the pivot (Ccur) and after the move (Cnxt), k = 1 .. NB-1 (0 past
+    // N-1); slot k = 0 holds ceil(N/2) in one buffer and floor(N/2) in the
+    // other and is never rewritten (see the update of R_p above).
+    int32_t* Ccur = Cs;
+    int32_t* Cnxt = Cs + NB;
 #pragma unroll
     for (int q = 0; q < NW; ++q) Ccur[lane + 32 * q] = c[q];
+    if (lane == 0) {
+        Ccur[0] = N - N / 2;
+        Cnxt[0] = N / 2;
+    }
     __syncwarp();
+    const bool own_c0 = lane == 0;  // the lane whose k = lane + 32q is 0 at q = 0
     // correlation masks of the recomputation: i < N - k for k = lane + 32q
     uint32_t cmask[kRecompute ? NW : 1][kRecompute ? NW : 1];
     int32_t nk[NW];
@@ -369,11 +432,19 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
             for (int w = 0; w + q < NW; ++w) cmask[q][w] = word_lowmask(w, nk[q]);
         }
     }
+    // all-ones masks: bits 0 .. N-1, and every bit (the move's ranges below)
+    uint32_t allN[NW], allB[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        allN[w] = word_lowmask(w, N);
+        allB[w] = kFull;
+    }
     const int min_t = max_iter / 10;
     const int max_t = (12 * max_iter) / 100;
     const int64_t nsteps = budget < 0 ? max_iter : (budget < max_iter ? budget : max_iter);
     uint32_t rx = 0, ry = 0;
     int64_t steps = 0;
+    bool fault = false;
 
     for (int t = 1; t <= nsteps; ++t) {
         if (((t - 1) & 31) == 0) {  // draws of steps t .. t+31, one per lane
@@ -389,7 +460,7 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
         int32_t cand[NW], Mq[NW];
         int32_t kmin_l = INT_MAX;
 #pragma unroll
-        for (int q = 0; q < NW; ++q) {
+        for (int q = QB; q < QE; ++q) {
             int dm = 0;
 #pragma unroll
             for (int w = 0; w <= q && w + q < NW; ++w)
@@ -402,47 +473,80 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
             // E_j < 2^23 for N <= 256 and j < 256: (E_j, j) packs into 31 bits
             kmin_l = min(kmin_l, adm ? (Ej << 8) | (lane + 32 * q) : INT_MAX);
         }
-        const int32_t kmin = __reduce_min_sync(kFull, kmin_l);
-        if (kmin == INT_MAX) break;  // every move tabu and none aspirates
+        const int32_t kmin_w = __reduce_min_sync(kFull, kmin_l);
+        int eq = 0;  // this warp's admissible minimisers
+#pragma unroll
+        for (int q = QB; q < QE; ++q) eq += (cand[q] == (kmin_w >> 8)) ? 1 : 0;
+        const int count_w = kmin_w == INT_MAX ? 0 : __reduce_add_sync(kFull, eq);
+        int32_t kmin = kmin_w;
+        int count = count_w, count_lo = 0;  // count_lo: minimisers of the lower half (WPS = 2)
+        if constexpr (WPS == 2) {
+            uint64_t o = 0;
+            if (!pair_exchange(link, HALF, (*xseq)++,
+                               (static_cast<uint64_t>(count_w) << 31) | static_cast<uint32_t>(kmin_w), o, lane)) {
+                fault = true;
+                break;
+            }
+            const int32_t kmin_o = static_cast<int32_t>(o & 0x7FFFFFFFu);
+            const int count_o = static_cast<int>(o >> 31);
+            kmin = min(kmin_w, kmin_o);
+            // minimisers of either half: the same energy, whatever their index
+            const int cw = (kmin_w >> 8) == (kmin >> 8) ? count_w : 0;
+            const int co = (kmin_o >> 8) == (kmin >> 8) ? count_o : 0;
+            count = cw + co;
+            count_lo = HALF == 0 ? cw : co;
+        }
+        // Every move tabu and none aspirating: the search has no admissible
+        // move and stops.  The default maxIter keeps maxTabu below N, so only a
+        // user maxIter of about 8N or more (maxTabu >= N) gets here.
+        if (kmin == INT_MAX) break;
         const int32_t m = kmin >> 8;
         int p = kmin & 255;  // lowest admissible minimiser
         {
-            int eq = 0;
-#pragma unroll
-            for (int q = 0; q < NW; ++q) eq += (cand[q] == m) ? 1 : 0;
-            const int count = __reduce_add_sync(kFull, eq);
             int idx = count > 1 ? static_cast<int>((static_cast<uint64_t>(u_tie) * count) >> 32) : 0;
             if (idx > 0) {  // the idx-th minimiser in ascending j
-                bool found = false;
+                bool mine = true;  // WPS = 2: the warp holding it finds it, then tells the other
+                if constexpr (WPS == 2) {
+                    mine = HALF == 0 ? idx < count_lo : idx >= count_lo;
+                    if (HALF == 1) idx -= count_lo;
+                }
+                if (mine) {
+                    bool found = false;
 #pragma unroll
-                for (int q = 0; q < NW; ++q) {
-                    const uint32_t tb = __ballot_sync(kFull, cand[q] == m);
-                    const int pc_q = __popc(tb);
-                    if (!found) {
-                        if (idx < pc_q) {
-                            p = 32 * q + nth_set_bit(tb, idx);
-                            found = true;
-                        } else {
-                            idx -= pc_q;
+                    for (int q = QB; q < QE; ++q) {
+                        const uint32_t tb = __ballot_sync(kFull, cand[q] == m);
+                        const int pc_q = __popc(tb);
+                        if (!found) {
+                            if (idx < pc_q) {
+                                p = 32 * q + nth_set_bit(tb, idx);
+                                found = true;
+                            } else {
+                                idx -= pc_q;
+                            }
                         }
                     }
+                }
+                if constexpr (WPS == 2) {
+                    uint64_t o = 0;
+                    if (!pair_exchange(link, HALF, (*xseq)++, mine ? static_cast<uint64_t>(p) : 0u, o, lane)) {
+                        fault = true;
+                        break;
+                    }
+                    if (!mine) p = static_cast<int>(o);
                 }
             }
         }
         // ---- the move p: its windows (before the flip; bits k >= 1 are the
         // same after it), s_p, and the ranges k in [1, N-1-p] and [1, p]
         uint32_t Xp[NW], Yp[NW], mu[NW], mv[NW];
-        shr_uniform<NW>(B, p, Xp);
-        shr_uniform<NW>(RL, NB - 1 - p, Yp);
+        shr_uniform2<NW>(B, allN, p, Xp, mu);            // mu: bits 0 .. N-1-p
+        shr_uniform2<NW>(RL, allB, NB - 1 - p, Yp, mv);  // mv: bits 0 .. p
+        mu[0] &= ~1u;
+        mv[0] &= ~1u;
         const int32_t sp2 = (Xp[0] & 1u) ? 2 : -2;  // 2 s_p
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            mu[w] = word_lowmask(w, N - p) & (w == 0 ? ~1u : kFull);
-            mv[w] = word_lowmask(w, p + 1) & (w == 0 ? ~1u : kFull);
-        }
         int32_t dq[NW], c0[NW];
 #pragma unroll
-        for (int q = 0; q < NW; ++q) {
+        for (int q = QB; q < QE; ++q) {
             dq[q] = abs(p - (lane + 32 * q));
             c0[q] = Ccur[dq[q]];  // C_d before the move
         }
@@ -467,10 +571,11 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
             }
         }
 #pragma unroll
-        for (int q = 0; q < NW; ++q) Cnxt[lane + 32 * q] = c[q];
+        for (int q = 0; q < NW; ++q)
+            if (q > 0 || !own_c0) Cnxt[lane + 32 * q] = c[q];
         __syncwarp();
 #pragma unroll
-        for (int q = 0; q < NW; ++q) {
+        for (int q = QB; q < QE; ++q) {
             const int j = lane + 32 * q;
             const int32_t c1 = Cnxt[dq[q]];  // C'_d
             // crossed pairs: (p+k, j-k) for k <= min(N-1-p, j) and
@@ -482,10 +587,8 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
 #pragma unroll
             for (int w = 0; w + q < NW; ++w) words[q + 1 + w] = (Yp[w] ^ XB[q + w]) & mv[w] & mX[q + w];
             const int32_t F = min(N - 1 - p, j) + min(p, N - 1 - j) - 2 * csa_popc<NW + 1, 1>(words);
-            const int32_t sj2 = (XB[q] & 1u) ? 2 : -2;
-            const int32_t Rj = R[q] - sp2 * (c0[q] + c1 + F) - sj2;
-            const int32_t Rp = R[q] - sp2 * (N - 1 + 2 * Mq[q]);
-            R[q] = (j == p) ? Rp : Rj;
+            const int32_t sj2 = (XB[q] & 1u) ? 2 : -2;  // 2 s'_j
+            R[q] -= sp2 * (c0[q] + c1 + F) + sj2;
         }
         {
             int32_t* tmp = Ccur;
@@ -494,7 +597,7 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
         }
         const int32_t expiry = t + rand_int(min_t, max_t, u_ten);
 #pragma unroll
-        for (int q = 0; q < NW; ++q)
+        for (int q = QB; q < QE; ++q)
             if (lane + 32 * q == p) tabu[q] = expiry;
         E = m;
         if (m < E_best) {
@@ -505,7 +608,7 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
         ++steps;
         if constexpr (TRACE) {
             if (trace_len < trace_cap) {
-                if (lane == 0) trace[trace_len] = make_int4(static_cast<int>(g), t, p, m);
+                if (lane == 0 && HALF == 0) trace[trace_len] = make_int4(static_cast<int>(g), t, p, m);
                 ++trace_len;
             }
         }
@@ -516,6 +619,7 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
     TabuOut out;
     out.steps = steps;
     out.E_best = E_best;
+    out.fault = fault;
     return out;
 }
 

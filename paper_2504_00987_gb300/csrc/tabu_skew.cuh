@@ -216,6 +216,7 @@ __device__ TabuOut tabu_search_skew(uint32_t (&seq)[NW], const int N, const uint
     TabuOut out;
     out.steps = steps;
     out.E_best = E_best;
+    out.fault = false;  // one warp per search: nothing to lose step with
     return out;
 }
 

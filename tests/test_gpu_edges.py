@@ -68,3 +68,26 @@ def test_energy_batch_one_million_sampled(labs, orc):
     # every energy is consistent with the parity of C_k: E = sum C_k^2 with C_k = N-k mod 2
     floor = sum(1 for k in range(1, N) if (N - k) % 2)
     assert int(E.min()) >= floor
+
+
+@pytest.mark.parametrize("N", [13, 37, 70, 130])
+def test_long_tabu_search_can_run_out_of_moves(labs, orc, N):
+    """With a user maxIter of 20 N the tenure bound floor(12 maxIter / 100)
+    exceeds N, so every move can be tabu with none aspirating; the search then
+    stops early (Alg. 2 has no admissible move).  The GPU stops at the same
+    step as the oracle, with the same trajectory, and some search does stop."""
+    B, mi = 16, 20 * N
+    rng = np.random.default_rng(N)
+    starts = rng.integers(0, 1 << 63, size=(B, (N + 63) // 64), dtype=np.int64).astype(np.uint64)
+    for w in range((N + 63) // 64):
+        hi = N - 64 * w
+        if hi < 64:
+            starts[:, w] &= np.uint64((1 << max(hi, 0)) - 1)
+    out = labs.tabu_run(torch.from_numpy(starts.view(np.int64)).cuda(), N, seed=3, max_iter=mi, trace_cap=mi)
+    early = 0
+    for b in range(B):
+        best, bestE, steps, tr = orc.tabu_run(starts[b], N, 3, b, 0, max_iter=mi, trace_cap=mi)
+        assert int(out["steps"][b]) == steps and int(out["bestE"][b]) == bestE
+        assert np.array_equal(out["trace"][b, :steps].cpu().numpy(), tr)
+        early += steps < mi
+    assert early > 0
