@@ -8,9 +8,13 @@ flip-evals = tabu steps x N; pair-terms = flip-evals x (N-1).
 
     python bench.py [--gpus G] [--steps S] [--warmup W] [--impl gpu|reference]
 
+The same line carries the N = 92..120 configuration as extra keys: its
+throughput per N and its time to target (p50/p99 per N over 50 seeds).
+
 Under torchrun each rank runs its own 1,024 replicas (instances offset by
-rank x 1,024; weak scaling, no collective on the data path).  Rank 0 prints
-one JSON line.  `--impl reference` times the CPU oracle (test
+rank x 1,024; weak scaling, no collective on the data path); for time to
+target the ranks share the stop flag between slices of generations.  Rank 0
+prints one JSON line.  `--impl reference` times the CPU oracle (test
 infrastructure) on the host cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -725,22 +729,32 @@ def run_batch(args) -> None:
     t0 = time.perf_counter()
     mapping = labs.autotune(inst)
     tune_s = time.perf_counter() - t0
-    with labs.Batch(inst, mapping=mapping) as b:
-        for _ in range(args.warmup):
-            b.launch()
-        torch.cuda.synchronize()
-        ms_list = [timed_launch(torch, lambda: b.launch(stream), stream)[0] for _ in range(args.steps)]
-    ms = parallel.max_over_ranks(pg, [statistics.mean(ms_list)], dev)[0]
+    def makespan(m, steps):
+        with labs.Batch(inst, mapping=m) as b:
+            for _ in range(args.warmup):
+                b.launch()
+            torch.cuda.synchronize()
+            return statistics.mean(timed_launch(torch, lambda: b.launch(stream), stream)[0] for _ in range(steps))
+
+    ms = parallel.max_over_ranks(pg, [makespan(mapping, args.steps)], dev)[0]
     total_flips = parallel.sum_over_ranks(pg, [float(flips)], dev)[0]
-    # plain form: one launch per instance, back to back, on every 16th instance
-    sample = wl[::16]
+    # other mappings, for the record: one and two warps per replica
+    grid = []
+    for wps in (1, 2):
+        for wpb, bps in ((wps, 1), (wps, 2), (4, 1), (4, 2)):
+            m = {"warps_per_block": wpb, "blocks_per_sm": bps, "order": 0, "warps_per_seq": wps}
+            grid.append({**m, "ms": parallel.max_over_ranks(pg, [makespan(m, 3)], dev)[0]})
+    # plain form: one launch per instance, round robin over 128 streams (the
+    # kernels a GPU runs at once), every instance of the batch
+    streams = [torch.cuda.Stream() for _ in range(128)]
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    for x in sample:
-        labs.mts_launch(labs.make_params(x.N, x.K, max_steps=x.max_steps), x.seed, x.instance, 1)
+    for i, x in enumerate(wl):
+        labs.mts_launch(labs.make_params(x.N, x.K, max_steps=x.max_steps), x.seed, x.instance, 1,
+                        stream=streams[i % len(streams)])
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - t1
-    plain_rate = sum(x.max_steps * x.N for x in sample) / plain_s
+    plain_rate = flips / plain_s
     if rank == 0:
         value = total_flips / (ms / 1e3)
         print(json.dumps({
@@ -749,7 +763,9 @@ def run_batch(args) -> None:
             "scaling": "strong", "dtype": "int32", "data": "synthetic",
             "config": {"workload": "batch_uneven_512: N~U{40..127}, K~U{50..200}, 10 N^2 steps, seed 7",
                        "mapping": mapping, "autotune_s": tune_s},
-            "plain_one_launch_per_instance": {"flip_evals_per_s": plain_rate, "sample": len(sample)},
+            "mappings_ms": grid,
+            "plain_one_launch_per_instance": {"flip_evals_per_s": plain_rate, "instances": len(wl),
+                                              "streams": len(streams), "wall_s": plain_s},
             "speedup_vs_plain": value / plain_rate}), flush=True)
 
 
@@ -776,10 +792,14 @@ def run_serve(args) -> None:
 
     insts = [instance(i, r) for i, r in enumerate(reqs)]
 
-    def drive(submit, poll):
+    def drive(submit, poll, running=None):
         done, pending, i = {}, [], 0
         t0 = time.perf_counter()
+        samples, t_sample = [], 0.0
         while len(done) < len(reqs):
+            if running is not None and time.perf_counter() - t_sample > 0.01:
+                t_sample = time.perf_counter()
+                samples.append(running())
             now = time.perf_counter() - t0
             while i < len(reqs) and reqs[i].arrival_s <= now:
                 pending.append((i, submit(i), t0 + reqs[i].arrival_s))
@@ -793,20 +813,26 @@ def run_serve(args) -> None:
                     done[k] = (res, time.perf_counter() - t_arr)
             pending = keep
             time.sleep(0.0002)
+        drive.in_flight = samples
         return done, time.perf_counter() - t0
 
     qsteps = args.quantum_steps if args.quantum_us == 0 else (1 << 40)
     with labs.Server(max_slots=args.slots or 4096, max_N=160, max_K=100, quantum_steps=qsteps,
-                     quantum_us=args.quantum_us) as srv:
-        done, wall = drive(lambda i: srv.submit(insts[i]), srv.poll)
+                     quantum_us=args.quantum_us, warps_per_request=args.warps_per_request) as srv:
+        done, wall = drive(lambda i: srv.submit(insts[i]), srv.poll, lambda: srv.stats()["running"])
         st = srv.stats()
+    in_flight = drive.in_flight
     lat = np.array([done[k][1] for k in range(len(reqs))])
     tmode = np.array([r.target_mode for r in reqs])
     missed = sum(1 for k, r in enumerate(reqs) if r.target_mode and done[k][0]["status"] != labs.RUN_REACHED)
     served_rate = st["flip_evals"] / wall
-    # one launch per request, 64 streams round robin, on a prefix of the same stream
+    # one launch per request on a prefix of the same stream, round robin over as many
+    # streams as the service had requests in flight on average (at most 128, the
+    # number of kernels a GPU runs concurrently)
     nb = min(len(reqs), args.baseline_requests)
-    streams = [torch.cuda.Stream() for _ in range(64)]
+    mean_in_flight = float(np.mean(in_flight)) if in_flight else 1.0
+    n_streams = int(min(128, max(1, round(mean_in_flight))))
+    streams = [torch.cuda.Stream() for _ in range(n_streams)]
     outs, evs = {}, {}
 
     def submit_plain(i):
@@ -843,8 +869,13 @@ def run_serve(args) -> None:
                           "p50_cap_mode": float(np.percentile(lat[~tmode], 50)) if (~tmode).any() else None,
                           "p99_cap_mode": float(np.percentile(lat[~tmode], 99)) if (~tmode).any() else None},
             "target_misses": missed, "wall_s": wall, "gpu_busy_s": st["gpu_seconds"], "quanta": st["quanta"],
+            "in_flight": {"mean": mean_in_flight, "max": int(max(in_flight)) if in_flight else 0},
+            "warps_per_request": args.warps_per_request, "pair_quanta": st["pair_quanta"],
+            "admission_held_back": {"slots": st["deferred_slots"], "shared_memory": st["deferred_smem"],
+                                    "arena": st["deferred_hbm"]},
+            "arena_bytes": st["arena_bytes"],
             "plain_one_launch_per_request": {
-                "requests": nb, "flip_evals_per_s": flips_b / wall_b,
+                "requests": nb, "streams": n_streams, "flip_evals_per_s": flips_b / wall_b,
                 "latency_p50_s": float(np.percentile(lat_b, 50)),
                 "latency_p99_s": float(np.percentile(lat_b, 99))},
         }), flush=True)
@@ -912,6 +943,8 @@ def main() -> None:
     ap.add_argument("--baseline-requests", type=int, default=400, help="serve: plain-form prefix")
     ap.add_argument("--slots", type=int, default=0, help="serve: resident slots")
     ap.add_argument("--quantum-steps", type=int, default=2000, help="serve: tabu steps per slot per quantum")
+    ap.add_argument("--warps-per-request", type=int, default=1,
+                    help="serve: 1 = one warp per request, 2 = warp pairs while they fit")
     ap.add_argument("--quantum-us", type=int, default=4000,
                     help="serve: device-time budget per slot per quantum (0: the step count instead)")
     args = ap.parse_args()

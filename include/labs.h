@@ -77,6 +77,10 @@ extern "C" {
 #define LABS_RUN_REACHED 1 /* E(best) <= target_E */
 #define LABS_RUN_STOPPED 2 /* another replica of the same run reached target_E (GLF) */
 #define LABS_RUN_BADSTATE 3 /* labs_mts_resume: the state record belongs to another run */
+#define LABS_RUN_SYNC_LOST 4 /* a replica mapped on two warps (labs_mapping.warps_per_seq
+                                = 2) stopped because one warp waited for the other
+                                beyond a bounded number of polls; its record is not a
+                                result (never expected; reported instead of waiting) */
 
 typedef void* labs_stream_t; /* a cudaStream_t */
 
@@ -103,8 +107,12 @@ typedef void* labs_stream_t; /* a cudaStream_t */
  * randInt(floor(maxIter/10), floor(12 maxIter/100)); a bit is admissible iff
  * its tabu has expired or flipping it beats the search's best (aspiration);
  * ties for the admissible minimum are broken by the tie draw in ascending
- * bit order.  The child replaces a member (replace_policy) and the replica's
- * best on a strictly lower energy.
+ * bit order.  A search with no admissible move stops at that step: this
+ * cannot happen under the default maxIter (its tenure bound stays below N),
+ * but a user max_iter of about 8N or more lets floor(12 maxIter/100) reach
+ * N, and then every bit can be tabu with none aspirating.  The child
+ * replaces a member (replace_policy) and the replica's best on a strictly
+ * lower energy.
  */
 typedef struct labs_params {
     int32_t N;               /* 3 .. LABS_MAX_N */
@@ -185,10 +193,15 @@ typedef struct labs_instance {
 
 /* How a batch is mapped on the GPU. */
 typedef struct labs_mapping {
-    int32_t warps_per_block; /* populations (one per warp) per CTA: 1, 2, 4 or 8 */
+    int32_t warps_per_block; /* warps per CTA: 1, 2, 4 or 8 */
     int32_t blocks_per_sm;   /* resident CTAs per SM of the persistent grid, >= 1 */
     int32_t order;           /* LABS_ORDER_* */
-    int32_t pad;
+    int32_t warps_per_seq;   /* warps per replica: 1 (or 0), or 2 (warps_per_block 2, 4
+                                or 8): the two warps of a replica split every tabu
+                                step's neighbours and meet once per step in shared
+                                memory, which halves the serial chain of a step's
+                                scoring; a lost step (a bounded wait that runs out)
+                                stops the replica with LABS_RUN_SYNC_LOST */
 } labs_mapping;
 
 typedef struct labs_batch labs_batch; /* opaque */
@@ -325,15 +338,16 @@ int32_t labs_philox_batch(uint64_t seed, const uint32_t* d_ctr, int64_t B, uint3
 
 /*
  * Batched uneven instances: one persistent launch, captured once in a CUDA
- * graph, in which every warp takes the next instance from a device queue
- * and runs it to its stop condition.  Every instance must be bounded by a
+ * graph, in which every replica unit (one warp, or a pair of warps with
+ * warps_per_seq = 2) takes the next instance from a device queue and runs
+ * it to its stop condition.  Every instance must be bounded by a
  * generation budget or a step budget (with max_iter != 0).
  *
  * labs_autotune      -- picks a mapping for these instances by timing the
- *                       candidate mappings (warps_per_block x blocks_per_sm
- *                       within occupancy) on a copy of the batch with every
- *                       budget divided by 8; caches the choice per batch
- *                       signature.  BLOCKING; uses `stream`.
+ *                       candidate mappings (warps_per_seq x warps_per_block x
+ *                       blocks_per_sm within occupancy) on a copy of the
+ *                       batch with every budget divided by 8; caches the
+ *                       choice per batch signature.  BLOCKING; uses `stream`.
  * labs_batch_create  -- validates and orders the instances (host h_inst[n]),
  *                       uploads them, allocates the results and captures the
  *                       launch in a CUDA graph.  mapping == NULL: autotune.
@@ -363,14 +377,17 @@ int32_t labs_mts_batch_run(const labs_instance* h_inst, int64_t n, const labs_ma
 /*
  * Solve service: continuous batching of solve requests on one GPU.
  *
- * A server owns a device arena of `max_slots` slots.  A scheduler thread
- * admits pending requests (FIFO) into free slots as slots and memory free
- * up -- a request is admitted when a slot is free, its population fits the
- * HBM budget and its shared-memory footprint fits the quantum kernel -- and
- * runs quanta: one bounded launch in which every admitted request advances
- * by whole generations up to `quantum_steps` tabu steps, its population
- * staying in device memory between quanta.  Requests that arrive while a
- * quantum runs join at the next quantum.  A request's result is the same
+ * A server owns `max_slots` slots and a device arena for the populations.
+ * A scheduler thread admits pending requests (FIFO) as slots and memory free
+ * up -- a request is admitted when a slot is free, its word class (the
+ * kernel's word count for its N) still fits in one resident wave of the
+ * quantum kernels, by their shared memory and registers per SM, and the
+ * arena has a free extent of its footprint -- and runs quanta: one bounded
+ * launch per word class (each with that class's shared memory per warp, on
+ * its own stream) in which every admitted request advances by whole
+ * generations up to `quantum_steps` tabu steps, its population staying in
+ * its arena extent between quanta.  Requests that arrive while a quantum
+ * runs join at the next quantum.  A request's result is the same
  * alone, in any mix, under any quantum size (it is the labs_mts_launch run
  * of its instance).  Results carry the request's latency (submit -> result)
  * in labs_result.seconds.
@@ -382,13 +399,28 @@ typedef struct labs_serve_opts {
     int32_t warps_per_block;    /* quantum kernel CTA size in warps: 1, 2, 4 or 8 */
     int64_t quantum_steps;      /* tabu steps per slot per quantum (rounded up to a generation) */
     int64_t queue_capacity;     /* pending requests; submit answers LABS_EBUSY beyond it */
-    int64_t hbm_budget_bytes;   /* cap on the populations resident at once; 0: no cap */
+    int64_t hbm_budget_bytes;   /* bytes of the device arena holding the resident
+                                   populations; a request takes K (nw + 1) 4 bytes of it
+                                   (nw = 2, 3, 4, 5, 6, 8 for N up to 64, 96, 128, 160,
+                                   192, 256; padded to 16) while it runs, and waits in the
+                                   queue while no free extent fits it.  0: max_slots
+                                   requests of (max_N, max_K).  LABS_EINVAL if it holds no
+                                   (max_N, max_K) request. */
     int64_t quantum_timeout_ms; /* longest wait for one quantum before the server fails with
                                    LABS_ETIMEOUT; 0: 60000 */
     int64_t quantum_us;         /* > 0: a slot also suspends at the first generation boundary
                                    after this many microseconds of the quantum (device clock;
                                    at least one generation per quantum), so slots of every N
                                    share a quantum evenly; 0: steps only */
+    int32_t warps_per_request;  /* 0 or 1: one warp per request.  2: a quantum runs each
+                                   request whose word count is even on two warps (they split
+                                   every tabu step's neighbours) whenever all active requests
+                                   fit in one resident wave that way, else on one.  Results
+                                   do not depend on it.  On GB300, N <= 160, pairs measured
+                                   slower than single warps (the per-step exchange and the
+                                   duplicated move bookkeeping cost more than the halved
+                                   scoring saves), hence the default. */
+    int32_t pad;
 } labs_serve_opts;
 
 /* One solve request: an MTS instance; max_steps or max_generations must bound it. */
@@ -401,6 +433,14 @@ typedef struct labs_serve_stats {
     double gpu_seconds;         /* summed quantum durations */
     int32_t failed;             /* LABS_OK or the error that stopped the server */
     int32_t pad;
+    /* requests the admission rules held back, each request counted once per
+       rule: no free slot; its word class would not fit in one resident wave
+       of the quantum kernels (shared memory and registers per SM, from the
+       occupancy API; a request is always admitted when nothing runs); no free
+       arena extent of its footprint */
+    int64_t deferred_slots, deferred_smem, deferred_hbm;
+    int64_t arena_bytes, arena_used_bytes;
+    int64_t pair_quanta;        /* quanta that ran even-word-count requests on warp pairs */
 } labs_serve_stats;
 
 typedef struct labs_server labs_server; /* opaque */

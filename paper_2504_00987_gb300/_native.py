@@ -32,6 +32,7 @@ RUN_BUDGET = 0
 RUN_REACHED = 1
 RUN_STOPPED = 2
 RUN_BADSTATE = 3
+RUN_SYNC_LOST = 4
 
 # Every symbol include/labs.h declares.
 EXPORTED = [
@@ -137,7 +138,7 @@ class Mapping(ctypes.Structure):
         ("warps_per_block", ctypes.c_int32),
         ("blocks_per_sm", ctypes.c_int32),
         ("order", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("warps_per_seq", ctypes.c_int32),
     ]
 
 
@@ -152,6 +153,8 @@ class ServeOpts(ctypes.Structure):
         ("hbm_budget_bytes", ctypes.c_int64),
         ("quantum_timeout_ms", ctypes.c_int64),
         ("quantum_us", ctypes.c_int64),
+        ("warps_per_request", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
     ]
 
 
@@ -167,6 +170,12 @@ class ServeStats(ctypes.Structure):
         ("gpu_seconds", ctypes.c_double),
         ("failed", ctypes.c_int32),
         ("pad", ctypes.c_int32),
+        ("deferred_slots", ctypes.c_int64),
+        ("deferred_smem", ctypes.c_int64),
+        ("deferred_hbm", ctypes.c_int64),
+        ("arena_bytes", ctypes.c_int64),
+        ("arena_used_bytes", ctypes.c_int64),
+        ("pair_quanta", ctypes.c_int64),
     ]
 
 

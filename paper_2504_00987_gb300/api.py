@@ -189,11 +189,12 @@ def _mapping(mapping):
     if isinstance(mapping, nat.Mapping):
         return mapping
     return nat.Mapping(int(mapping["warps_per_block"]), int(mapping["blocks_per_sm"]),
-                       int(mapping.get("order", nat.ORDER_LPT)), 0)
+                       int(mapping.get("order", nat.ORDER_LPT)), int(mapping.get("warps_per_seq", 1)))
 
 
 def _mapping_dict(m: nat.Mapping) -> dict:
-    return {"warps_per_block": m.warps_per_block, "blocks_per_sm": m.blocks_per_sm, "order": m.order}
+    return {"warps_per_block": m.warps_per_block, "blocks_per_sm": m.blocks_per_sm, "order": m.order,
+            "warps_per_seq": max(1, m.warps_per_seq)}
 
 
 def _result_dicts(res, n, with_N=True):
@@ -286,9 +287,10 @@ class Server:
     def __init__(self, max_slots: int = 1024, max_N: int = 256, max_K: int = 128,
                  warps_per_block: int = 4, quantum_steps: int = 2000,
                  queue_capacity: int = 1 << 20, hbm_budget_bytes: int = 0,
-                 quantum_timeout_ms: int = 0, quantum_us: int = 0):
+                 quantum_timeout_ms: int = 0, quantum_us: int = 0, warps_per_request: int = 0):
         opts = nat.ServeOpts(max_slots, max_N, max_K, warps_per_block, quantum_steps,
-                             queue_capacity, hbm_budget_bytes, quantum_timeout_ms, quantum_us)
+                             queue_capacity, hbm_budget_bytes, quantum_timeout_ms, quantum_us,
+                             warps_per_request, 0)
         L = nat.load()
         self._h = L.labs_serve_create(ctypes.byref(opts))
         if not self._h:

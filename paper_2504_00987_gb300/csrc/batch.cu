@@ -1,13 +1,14 @@
 // batch.cu -- many independent MTS instances of uneven N, K and budget in
 // one persistent launch.  The grid is sized to stay resident (blocks_per_sm
-// CTAs of warps_per_block warps on every SM); each warp takes the next
-// instance from a device-wide queue (one atomicAdd per instance, ordered
-// longest first by the host), runs it to its stop condition with the
-// replica engine and writes its result at the instance's original index.
-// Instances of different word counts share the launch: the warp dispatches
-// on W = ceil(N/64) per instance.  Per-instance results do not depend on
-// the mapping or on the other instances (every draw is keyed by the
-// instance's own seed and instance number).
+// CTAs of warps_per_block warps on every SM); each replica unit (one warp,
+// or with warps_per_seq = 2 a pair of warps that split every step's
+// neighbours) takes the next instance from a device-wide queue (one
+// atomicAdd per instance, ordered longest first by the host), runs it to
+// its stop condition with the replica engine and writes its result at the
+// instance's original index.  Instances of different word counts share the
+// launch: the unit dispatches on W = ceil(N/64) per instance.  Per-instance
+// results do not depend on the mapping or on the other instances (every
+// draw is keyed by the instance's own seed and instance number).
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -32,72 +33,110 @@ __device__ __forceinline__ ReplicaCfg cfg_from_instance(const labs_instance& in)
     return c;
 }
 
-template <int NW>
+template <int NW, int WPS, int HALF>
 __device__ __forceinline__ void run_instance(const ReplicaCfg& cfg, unsigned char* base,
-                                             labs_device_result* out, int lane) {
+                                             labs_device_result* out, int lane, PairLink* link,
+                                             uint32_t* xseq) {
     uint32_t* pop = reinterpret_cast<uint32_t*>(base);
     int32_t* popE = reinterpret_cast<int32_t*>(pop + cfg.K * NW);
     int32_t* Cs = popE + cfg.K;
-    replica_run<NW>(cfg, pop, popE, Cs, nullptr, 0, nullptr, out, lane);
+    replica_run<NW, false, false, WPS, HALF>(cfg, pop, popE, Cs, nullptr, 0, nullptr, out, lane, link, xseq);
 }
 
-template <int NWMAX>
-__global__ void __launch_bounds__(256) batch_kernel(const BatchArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    unsigned char* base = smem + static_cast<size_t>(warp) * a.smem_per_warp;
+// The queue loop of one unit.  WPS = 2: half 0 takes the instance and tells
+// half 1 through the pair's link; both then run it.
+template <int NWMAX, int WPS, int HALF>
+__device__ __forceinline__ void batch_unit(const BatchArgs& a, unsigned char* base, int lane, PairLink* link) {
+    uint32_t xseq = 1;  // exchange 0 would match the zeroed link words
     for (;;) {
         unsigned long long idx = 0;
-        if (lane == 0) idx = atomicAdd(a.queue, 1ull);
-        idx = __shfl_sync(kFull, idx, 0);
+        if (HALF == 0) {
+            if (lane == 0) idx = atomicAdd(a.queue, 1ull);
+            idx = __shfl_sync(kFull, idx, 0);
+        }
+        if constexpr (WPS == 2) {
+            uint64_t o = 0;
+            if (!pair_exchange(link, HALF, xseq++, HALF == 0 ? idx : 0u, o, lane)) break;
+            if (HALF == 1) idx = o;
+        }
         if (idx >= static_cast<unsigned long long>(a.n)) break;
         const labs_instance in = a.inst[idx];
         const ReplicaCfg cfg = cfg_from_instance(in);
         labs_device_result* out = a.out + a.order[idx];
         const int W = (in.N + 63) / 64;
         if (W == 1) {
-            run_instance<2>(cfg, base, out, lane);
+            run_instance<2, WPS, HALF>(cfg, base, out, lane, link, &xseq);
         } else if (W == 2) {
             // four words up to N = 128: a three-word path in this kernel cost the
             // four-word one its registers (172 -> 128) and the batch's makespan,
             // which the longest (largest-N) instances set, 12 % on GB300
-            if constexpr (NWMAX >= 4) run_instance<4>(cfg, base, out, lane);
+            if constexpr (NWMAX >= 4) run_instance<4, WPS, HALF>(cfg, base, out, lane, link, &xseq);
         } else if (W == 3) {
-            if constexpr (NWMAX >= 6) run_instance<6>(cfg, base, out, lane);
+            if constexpr (NWMAX >= 6) run_instance<6, WPS, HALF>(cfg, base, out, lane, link, &xseq);
         } else {
-            if constexpr (NWMAX >= 8) run_instance<8>(cfg, base, out, lane);
+            if constexpr (NWMAX >= 8) run_instance<8, WPS, HALF>(cfg, base, out, lane, link, &xseq);
         }
         __syncwarp();
     }
 }
 
-static const void* batch_fn(int nwmax) {
-    switch (nwmax) {
-        case 2: return reinterpret_cast<const void*>(&batch_kernel<2>);
-        case 4: return reinterpret_cast<const void*>(&batch_kernel<4>);
-        case 6: return reinterpret_cast<const void*>(&batch_kernel<6>);
-        default: return reinterpret_cast<const void*>(&batch_kernel<8>);
+// Pairs take as many registers as they need (see serve_quantum_kernel).
+template <int NWMAX, int WPS>
+__global__ void __launch_bounds__(256, WPS == 2 ? 1 : 0) batch_kernel(const BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PairLink links[8 / WPS];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    unsigned char* base = smem + static_cast<size_t>(warp) * a.smem_per_warp;
+    if constexpr (WPS == 1) {
+        batch_unit<NWMAX, 1, 0>(a, base, lane, nullptr);
+    } else {
+        PairLink* link = &links[warp >> 1];
+        if (lane < 4) reinterpret_cast<unsigned long long*>(link->slot)[lane] = 0ull;
+        __syncthreads();  // every link word is zero before either warp of a pair publishes
+        if (warp & 1)
+            batch_unit<NWMAX, 2, 1>(a, base, lane, link);
+        else
+            batch_unit<NWMAX, 2, 0>(a, base, lane, link);
     }
 }
 
-cudaError_t batch_prepare(int nwmax, int warps_per_block, size_t smem_per_warp, int* max_blocks_per_sm) {
-    const void* fn = batch_fn(nwmax);
+static const void* batch_fn(int nwmax, int wps) {
+    if (wps == 2) {
+        switch (nwmax) {
+            case 2: return reinterpret_cast<const void*>(&batch_kernel<2, 2>);
+            case 4: return reinterpret_cast<const void*>(&batch_kernel<4, 2>);
+            case 6: return reinterpret_cast<const void*>(&batch_kernel<6, 2>);
+            default: return reinterpret_cast<const void*>(&batch_kernel<8, 2>);
+        }
+    }
+    switch (nwmax) {
+        case 2: return reinterpret_cast<const void*>(&batch_kernel<2, 1>);
+        case 4: return reinterpret_cast<const void*>(&batch_kernel<4, 1>);
+        case 6: return reinterpret_cast<const void*>(&batch_kernel<6, 1>);
+        default: return reinterpret_cast<const void*>(&batch_kernel<8, 1>);
+    }
+}
+
+cudaError_t batch_prepare(int nwmax, int wps, int warps_per_block, size_t smem_per_warp, int* max_blocks_per_sm) {
+    const void* fn = batch_fn(nwmax, wps);
     const size_t smem = smem_per_warp * warps_per_block;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, fn, warps_per_block * 32, smem);
 }
 
-cudaError_t launch_batch(const BatchArgs& a, int nwmax, int blocks, int warps_per_block, cudaStream_t stream) {
+cudaError_t launch_batch(const BatchArgs& a, int nwmax, int wps, int blocks, int warps_per_block,
+                         cudaStream_t stream) {
+    if (wps == 2 && warps_per_block % 2 != 0) return cudaErrorInvalidValue;
     const size_t smem = a.smem_per_warp * warps_per_block;
-    switch (nwmax) {
-        case 2: batch_kernel<2><<<blocks, warps_per_block * 32, smem, stream>>>(a); break;
-        case 4: batch_kernel<4><<<blocks, warps_per_block * 32, smem, stream>>>(a); break;
-        case 6: batch_kernel<6><<<blocks, warps_per_block * 32, smem, stream>>>(a); break;
-        default: batch_kernel<8><<<blocks, warps_per_block * 32, smem, stream>>>(a); break;
-    }
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(blocks));
+    cfg.blockDim = dim3(static_cast<unsigned>(warps_per_block * 32));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    void* args[] = {const_cast<BatchArgs*>(&a)};
+    return cudaLaunchKernelExC(&cfg, batch_fn(nwmax, wps), args);
 }
 
 }  // namespace lgpu

@@ -94,10 +94,16 @@ std::vector<int32_t> queue_order(const labs_instance* h, int64_t n, int order) {
     return idx;
 }
 
+int wps_of(const labs_mapping& m) { return m.warps_per_seq == 2 ? 2 : 1; }
+
 int32_t check_mapping(const labs_mapping& m) {
     if (m.warps_per_block != 1 && m.warps_per_block != 2 && m.warps_per_block != 4 &&
         m.warps_per_block != 8)
         return fail(LABS_EINVAL, "warps_per_block must be 1, 2, 4 or 8");
+    if (m.warps_per_seq < 0 || m.warps_per_seq > 2)
+        return fail(LABS_EINVAL, "warps_per_seq must be 1 (or 0) or 2");
+    if (m.warps_per_seq == 2 && m.warps_per_block == 1)
+        return fail(LABS_EINVAL, "warps_per_seq = 2 needs warps_per_block 2, 4 or 8");
     if (m.blocks_per_sm < 1 || m.blocks_per_sm > 64) return fail(LABS_EINVAL, "blocks_per_sm outside 1..64");
     if (m.order != LABS_ORDER_LPT && m.order != LABS_ORDER_GIVEN) return fail(LABS_EINVAL, "unknown order");
     return LABS_OK;
@@ -178,7 +184,7 @@ int32_t labs_autotune(const labs_instance* h_inst, int64_t n, labs_stream_t stre
     if (out == nullptr) return fail(LABS_EINVAL, "out is NULL");
     LABS_TRY(validate_instances(h_inst, n));
     NvtxRange range("labs autotune");
-    labs_mapping best{4, 1, LABS_ORDER_LPT, 0};
+    labs_mapping best{4, 1, LABS_ORDER_LPT, 1};
     if (n == 0) {
         *out = best;
         return ok();
@@ -210,29 +216,32 @@ int32_t labs_autotune(const labs_instance* h_inst, int64_t n, labs_stream_t stre
     const lgpu::BatchArgs a = args_of(d, n, spw);
     const int sms = sm_count();
     float best_ms = 1e30f;
-    bool warmed = false;
-    for (int wpb : {1, 2, 4, 8}) {
-        int maxb = 0;
-        if (e == cudaSuccess) e = lgpu::batch_prepare(nwmax, wpb, spw, &maxb);
-        if (e != cudaSuccess) break;
-        for (int bps : {1, 2, 4, 8, 16}) {
-            if (bps > maxb) break;
-            // more resident warps than instances x 2 cannot help
-            if (bps > 1 && static_cast<int64_t>(sms) * (bps / 2) * wpb >= 2 * n) break;
-            for (int rep = warmed ? 0 : 1; rep >= 0 && e == cudaSuccess; --rep) {
-                e = cudaMemsetAsync(d.queue, 0, sizeof(unsigned long long), s);
-                if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-                if (e == cudaSuccess) e = lgpu::launch_batch(a, nwmax, sms * bps, wpb, s);
-                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            }
-            warmed = true;
-            float ms = 0;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    for (int wps : {1, 2}) {
+        bool warmed = false;  // each kernel family gets one untimed launch
+        for (int wpb : {1, 2, 4, 8}) {
+            if (wpb < wps) continue;
+            int maxb = 0;
+            if (e == cudaSuccess) e = lgpu::batch_prepare(nwmax, wps, wpb, spw, &maxb);
             if (e != cudaSuccess) break;
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = labs_mapping{wpb, bps, LABS_ORDER_LPT, 0};
+            for (int bps : {1, 2, 4, 8, 16}) {
+                if (bps > maxb) break;
+                // more resident replicas than instances x 2 cannot help
+                if (bps > 1 && static_cast<int64_t>(sms) * (bps / 2) * (wpb / wps) >= 2 * n) break;
+                for (int rep = warmed ? 0 : 1; rep >= 0 && e == cudaSuccess; --rep) {
+                    e = cudaMemsetAsync(d.queue, 0, sizeof(unsigned long long), s);
+                    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+                    if (e == cudaSuccess) e = lgpu::launch_batch(a, nwmax, wps, sms * bps, wpb, s);
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                }
+                warmed = true;
+                float ms = 0;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = labs_mapping{wpb, bps, LABS_ORDER_LPT, wps};
+                }
             }
         }
     }
@@ -276,7 +285,7 @@ int32_t labs_batch_create(const labs_instance* h_inst, int64_t n, const labs_map
     b->d_out = d.out;
     b->d_queue = d.queue;
     int maxb = 0;
-    if (e == cudaSuccess) e = lgpu::batch_prepare(b->nwmax, m.warps_per_block, b->smem_per_warp, &maxb);
+    if (e == cudaSuccess) e = lgpu::batch_prepare(b->nwmax, wps_of(m), m.warps_per_block, b->smem_per_warp, &maxb);
     if (e == cudaSuccess && maxb < 1) {
         labs_batch_destroy(b);
         return fail(LABS_EINVAL, "mapping does not fit on an SM (warps_per_block=%d)", m.warps_per_block);
@@ -287,7 +296,7 @@ int32_t labs_batch_create(const labs_instance* h_inst, int64_t n, const labs_map
     if (e == cudaSuccess) {
         cudaError_t le = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->cap);
         if (le == cudaSuccess)
-            le = lgpu::launch_batch(args_of(d, n, b->smem_per_warp), b->nwmax, b->blocks,
+            le = lgpu::launch_batch(args_of(d, n, b->smem_per_warp), b->nwmax, wps_of(m), b->blocks,
                                     m.warps_per_block, b->cap);
         e = cudaStreamEndCapture(b->cap, &b->graph);
         if (le != cudaSuccess) e = le;

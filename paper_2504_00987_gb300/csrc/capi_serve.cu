@@ -1,10 +1,14 @@
 // capi_serve.cu -- host side of the solve service (labs_serve_* in labs.h).
 //
 // One scheduler thread per server runs the loop
-//   admit pending requests into free slots (FIFO; a free slot, the HBM
-//   budget and the quantum kernel's shared memory must all have room) ->
-//   upload the new slots' records and the active list -> launch one quantum
-//   -> wait for it (bounded) -> harvest finished slots, free them.
+//   admit pending requests (FIFO) while a slot is free, the request's word
+//   class still fits in one resident wave of the GPU (shared memory and
+//   registers, from the occupancy API) and the HBM arena has a free extent
+//   of the request's footprint -> upload the new slots' records and the
+//   active list -> launch one quantum: one kernel per word-count class, each
+//   on its own stream and with its class's shared memory per warp -> wait
+//   for it (bounded) -> harvest finished slots, free their slots and
+//   extents.
 // Submitting, polling and cancelling only touch host state under the
 // server's mutex, so they never wait for the GPU.  Every wait is bounded:
 // the scheduler waits for new work with a timeout and for a quantum up to
@@ -17,6 +21,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -33,28 +38,90 @@ using Clock = std::chrono::steady_clock;
 namespace {
 
 enum TicketState { kPending = 0, kRunning = 1, kDone = 2, kCanceled = 3 };
+// admission rules that held a request back (each counted once per request)
+enum HeldBy { kHeldSlots = 1, kHeldHbm = 2, kHeldSmem = 4 };
+
+constexpr int kClasses = 6;
+constexpr int kClassNw[kClasses] = {2, 3, 4, 5, 6, 8};
+
+int class_of(int N) {
+    const int nw = lgpu::serve_class_nw(N);
+    for (int c = 0; c < kClasses; ++c)
+        if (kClassNw[c] == nw) return c;
+    return kClasses - 1;
+}
 
 struct Ticket {
     labs_request req{};
     int state = kPending;
     int32_t slot = -1;
+    int cls = -1;
+    int held = 0;
+    int64_t off = -1;  // bytes into the arena
     bool cancel_requested = false;
     labs_result res{};
     Clock::time_point t_submit;
 };
 
+// Arena bytes of a request: its population (K x nw words) and energies (K),
+// nw the word count its kernel uses, padded to 16.
 int64_t footprint(const labs_request& r) {
-    const int64_t nw = 2 * ((r.N + 63) / 64);
-    return static_cast<int64_t>(r.K) * nw * 4 + static_cast<int64_t>(r.K) * 4;
+    const int64_t nw = lgpu::serve_class_nw(r.N);
+    return (static_cast<int64_t>(r.K) * (nw + 1) * 4 + 15) & ~int64_t{15};
 }
+
+// First-fit allocator of extents of the device arena (byte offsets, 16-aligned).
+struct Arena {
+    std::map<int64_t, int64_t> free_ext;  // offset -> length
+    int64_t size = 0, used = 0;
+    void init(int64_t n) {
+        free_ext.clear();
+        free_ext[0] = n;
+        size = n;
+        used = 0;
+    }
+    int64_t alloc(int64_t n) {
+        for (auto it = free_ext.begin(); it != free_ext.end(); ++it) {
+            if (it->second < n) continue;
+            const int64_t off = it->first, len = it->second;
+            free_ext.erase(it);
+            if (len > n) free_ext[off + n] = len - n;
+            used += n;
+            return off;
+        }
+        return -1;
+    }
+    void release(int64_t off, int64_t n) {
+        used -= n;
+        auto it = free_ext.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_ext.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_ext.erase(nx);
+        }
+        if (it != free_ext.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_ext.erase(it);
+            }
+        }
+    }
+};
 
 }  // namespace
 
 struct labs_server {
     labs_serve_opts opts{};
     int device = 0;
-    int nwmax = 2;
-    size_t pop_stride_words = 0;
+    // per word-count class: shared memory per warp, warps resident in one wave
+    // (one warp per slot; two warps per slot, 0 where pairs do not apply), active slots
+    size_t cls_smem[kClasses] = {};
+    int64_t cls_cap[kClasses] = {};
+    int64_t cls_cap2[kClasses] = {};
+    int64_t cls_active[kClasses] = {};
+    int pair_wpb = 2;  // CTA size of the two-warps-per-slot launches
+    Arena arena;
 
     std::mutex mu;
     std::condition_variable cv;
@@ -66,13 +133,15 @@ struct labs_server {
     bool stop = false;
     int32_t failed = LABS_OK;
     std::string fail_msg;
-    int64_t resident_bytes = 0;
     labs_serve_stats stats{};
     std::thread th;
 
     cudaStream_t stream = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaStream_t cls_stream[kClasses] = {};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_fork = nullptr;
+    cudaEvent_t ev_join[kClasses] = {};
     labs_instance* d_cfg = nullptr;
+    int64_t* d_off = nullptr;
     lgpu::ServeState* d_state = nullptr;
     uint32_t* d_pop = nullptr;
     int32_t* d_active = nullptr;
@@ -81,6 +150,7 @@ struct labs_server {
     int64_t* d_used = nullptr;
     // pinned staging
     labs_instance* h_cfg = nullptr;
+    int64_t* h_off = nullptr;
     lgpu::ServeState* h_state = nullptr;
     int32_t* h_active = nullptr;
     labs_device_result* h_out = nullptr;
@@ -90,9 +160,55 @@ struct labs_server {
 
 namespace {
 
+// Fraction of one resident wave the active slots take, with `extra` more of class c.
+double wave_fraction(const labs_server* s, int c, int64_t extra) {
+    double f = 0.0;
+    for (int k = 0; k < kClasses; ++k) {
+        const int64_t n = s->cls_active[k] + (k == c ? extra : 0);
+        if (n > 0) f += static_cast<double>(n) / static_cast<double>(s->cls_cap[k]);
+    }
+    return f;
+}
+
+// True if every active slot of an even word class fits one resident wave on two warps
+// (and the others on one): the quantum then runs those slots on warp pairs.
+bool use_pairs(const labs_server* s) {
+    if (s->opts.warps_per_request != 2) return false;
+    double f = 0.0;
+    for (int k = 0; k < kClasses; ++k) {
+        const int64_t n = s->cls_active[k];
+        if (n == 0) continue;
+        f += s->cls_cap2[k] > 0 ? 2.0 * static_cast<double>(n) / static_cast<double>(s->cls_cap2[k])
+                                : static_cast<double>(n) / static_cast<double>(s->cls_cap[k]);
+    }
+    return f <= 1.0 + 1e-9;
+}
+
+void hold(labs_server* s, Ticket& t, int rule) {
+    if (t.held & rule) return;
+    t.held |= rule;
+    if (rule == kHeldSlots) s->stats.deferred_slots++;
+    if (rule == kHeldHbm) s->stats.deferred_hbm++;
+    if (rule == kHeldSmem) s->stats.deferred_smem++;
+}
+
+// A running request leaves: its slot, arena extent and class share are freed.
+void release_slot(labs_server* s, Ticket& t) {
+    s->slot_ticket[static_cast<size_t>(t.slot)] = 0;
+    s->free_slots.push_back(t.slot);
+    s->arena.release(t.off, footprint(t.req));
+    s->cls_active[t.cls]--;
+    s->stats.running--;
+    s->stats.arena_used_bytes = s->arena.used;
+}
+
 void free_server(labs_server* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
+    for (int c = 0; c < kClasses; ++c)
+        if (s->cls_stream[c]) cudaStreamSynchronize(s->cls_stream[c]);
     cudaFree(s->d_cfg);
+    cudaFree(s->d_off);
+    cudaFreeHost(s->h_off);
     cudaFree(s->d_state);
     cudaFree(s->d_pop);
     cudaFree(s->d_active);
@@ -107,6 +223,11 @@ void free_server(labs_server* s) {
     cudaFreeHost(s->h_used);
     if (s->ev0) cudaEventDestroy(s->ev0);
     if (s->ev1) cudaEventDestroy(s->ev1);
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    for (int c = 0; c < kClasses; ++c) {
+        if (s->ev_join[c]) cudaEventDestroy(s->ev_join[c]);
+        if (s->cls_stream[c]) cudaStreamDestroy(s->cls_stream[c]);
+    }
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -137,8 +258,9 @@ void scheduler(labs_server* s) {
     const int64_t timeout_ms = s->opts.quantum_timeout_ms > 0 ? s->opts.quantum_timeout_ms : 60000;
     std::vector<int32_t> fresh;
     std::vector<int32_t> active;
+    std::vector<int32_t> by_class[kClasses];
+    bool pairs = false;
     for (;;) {
-        size_t smem_per_warp = 16;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv.wait_for(lk, std::chrono::milliseconds(20), [&] {
@@ -152,42 +274,61 @@ void scheduler(labs_server* s) {
                 Ticket& t = s->tickets[id];
                 if (t.cancel_requested) {
                     t.state = kCanceled;
-                    s->slot_ticket[slot] = 0;
-                    s->free_slots.push_back(static_cast<int32_t>(slot));
-                    s->resident_bytes -= footprint(t.req);
-                    s->stats.running--;
+                    release_slot(s, t);
                     s->stats.canceled++;
                 }
             }
-            // admission: FIFO while a slot, the HBM budget and shared memory have room
+            // admission, FIFO: a free slot, room in one resident wave for the
+            // request's class (always, if nothing runs), a free arena extent
             fresh.clear();
-            while (!s->pending.empty() && !s->free_slots.empty()) {
+            while (!s->pending.empty()) {
                 const uint64_t id = s->pending.front();
                 Ticket& t = s->tickets[id];
-                const int64_t fp = footprint(t.req);
-                if (s->opts.hbm_budget_bytes > 0 && s->resident_bytes + fp > s->opts.hbm_budget_bytes &&
-                    s->stats.running > 0)
+                if (s->free_slots.empty()) {
+                    hold(s, t, kHeldSlots);
                     break;
+                }
+                const int c = class_of(t.req.N);
+                if (s->stats.running > 0 && wave_fraction(s, c, 1) > 1.0 + 1e-9) {
+                    hold(s, t, kHeldSmem);
+                    break;
+                }
+                const int64_t off = s->arena.alloc(footprint(t.req));
+                if (off < 0) {
+                    hold(s, t, kHeldHbm);
+                    break;
+                }
                 s->pending.pop_front();
                 const int32_t slot = s->free_slots.back();
                 s->free_slots.pop_back();
                 s->slot_ticket[static_cast<size_t>(slot)] = id;
                 t.state = kRunning;
                 t.slot = slot;
-                s->resident_bytes += fp;
+                t.cls = c;
+                t.off = off;
+                s->cls_active[c]++;
                 s->stats.running++;
                 s->stats.pending--;
+                s->stats.arena_used_bytes = s->arena.used;
                 s->h_cfg[slot] = t.req;
                 s->h_cfg[slot].p_mut_u32 = default_p_mut(t.req.N, t.req.p_mut_u32, t.req.variant);
+                s->h_off[slot] = off / 4;
                 fresh.push_back(slot);
             }
-            active.clear();
+            // the active slots, grouped by class (one launch per class)
+            for (auto& v : by_class) v.clear();
             for (size_t slot = 0; slot < s->slot_ticket.size(); ++slot)
-                if (s->slot_ticket[slot] != 0) {
-                    active.push_back(static_cast<int32_t>(slot));
-                    const labs_request& r = s->tickets[s->slot_ticket[slot]].req;
-                    smem_per_warp = std::max(smem_per_warp, lgpu::mts_smem_per_warp(r.N, r.K));
-                }
+                if (s->slot_ticket[slot] != 0)
+                    by_class[s->tickets[s->slot_ticket[slot]].cls].push_back(static_cast<int32_t>(slot));
+            pairs = use_pairs(s);
+            if (pairs) s->stats.pair_quanta++;
+        }
+        active.clear();
+        int seg_off[kClasses], seg_len[kClasses];
+        for (int c = 0; c < kClasses; ++c) {
+            seg_off[c] = static_cast<int>(active.size());
+            seg_len[c] = static_cast<int>(by_class[c].size());
+            active.insert(active.end(), by_class[c].begin(), by_class[c].end());
         }
         if (active.empty()) continue;
         NvtxRange range("labs serve quantum");
@@ -201,27 +342,41 @@ void scheduler(labs_server* s) {
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(s->d_state + slot, s->h_state + slot, sizeof(lgpu::ServeState),
                                     cudaMemcpyHostToDevice, s->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(s->d_off + slot, s->h_off + slot, sizeof(int64_t), cudaMemcpyHostToDevice,
+                                    s->stream);
             if (e != cudaSuccess) break;
         }
         const int n = static_cast<int>(active.size());
         std::copy(active.begin(), active.end(), s->h_active);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(s->d_active, s->h_active, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s->stream);
-        lgpu::ServeArgs a;
-        a.cfg = s->d_cfg;
-        a.state = s->d_state;
-        a.pop = s->d_pop;
-        a.pop_stride_words = s->pop_stride_words;
-        a.active = s->d_active;
-        a.n_active = n;
-        a.quantum_steps = s->opts.quantum_steps;
-        a.quantum_ns = static_cast<uint64_t>(s->opts.quantum_us) * 1000u;
-        a.out = s->d_out;
-        a.done = s->d_done;
-        a.quantum_used = s->d_used;
-        a.smem_per_warp = (smem_per_warp + 15) & ~static_cast<size_t>(15);
         if (e == cudaSuccess) e = cudaEventRecord(s->ev0, s->stream);
-        if (e == cudaSuccess) e = lgpu::launch_serve_quantum(a, s->nwmax, s->opts.warps_per_block, s->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(s->ev_fork, s->stream);
+        // one launch per class, each on its own stream, joined back into the main one
+        for (int c = 0; c < kClasses && e == cudaSuccess; ++c) {
+            if (seg_len[c] == 0) continue;
+            lgpu::ServeArgs a;
+            a.cfg = s->d_cfg;
+            a.state = s->d_state;
+            a.pop = s->d_pop;
+            a.pop_off = s->d_off;
+            a.active = s->d_active + seg_off[c];
+            a.n_active = seg_len[c];
+            a.quantum_steps = s->opts.quantum_steps;
+            a.quantum_ns = static_cast<uint64_t>(s->opts.quantum_us) * 1000u;
+            a.out = s->d_out + seg_off[c];
+            a.done = s->d_done + seg_off[c];
+            a.quantum_used = s->d_used + seg_off[c];
+            a.smem_per_warp = s->cls_smem[c];
+            const bool pair = pairs && s->cls_cap2[c] > 0;
+            e = cudaStreamWaitEvent(s->cls_stream[c], s->ev_fork, 0);
+            if (e == cudaSuccess)
+                e = lgpu::launch_serve_quantum(a, kClassNw[c], pair ? 2 : 1,
+                                               pair ? s->pair_wpb : s->opts.warps_per_block, s->cls_stream[c]);
+            if (e == cudaSuccess) e = cudaEventRecord(s->ev_join[c], s->cls_stream[c]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_join[c], 0);
+        }
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(s->h_done, s->d_done, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s->stream);
         if (e == cudaSuccess)
@@ -259,10 +414,7 @@ void scheduler(labs_server* s) {
             t.state = t.cancel_requested ? kCanceled : kDone;
             if (t.cancel_requested) s->stats.canceled++;
             else s->stats.completed++;
-            s->slot_ticket[static_cast<size_t>(slot)] = 0;
-            s->free_slots.push_back(slot);
-            s->resident_bytes -= footprint(t.req);
-            s->stats.running--;
+            release_slot(s, t);
         }
     }
 }
@@ -290,8 +442,13 @@ labs_server* labs_serve_create(const labs_serve_opts* o) {
         fail(LABS_EINVAL, "warps_per_block must be 1, 2, 4 or 8");
         return nullptr;
     }
-    if (lgpu::mts_smem_per_warp(o->max_N, o->max_K) * o->warps_per_block > 227u * 1024u) {
+    const int top = class_of(o->max_N);
+    if (lgpu::serve_smem_per_warp(kClassNw[top], o->max_K) * o->warps_per_block > 227u * 1024u) {
         fail(LABS_EINVAL, "max_N/max_K populations of one block exceed shared memory");
+        return nullptr;
+    }
+    if (o->warps_per_request < 0 || o->warps_per_request > 2) {
+        fail(LABS_EINVAL, "warps_per_request must be 0, 1 or 2");
         return nullptr;
     }
     if (o->quantum_steps < 1 || o->queue_capacity < 0 || o->hbm_budget_bytes < 0 ||
@@ -305,17 +462,52 @@ labs_server* labs_serve_create(const labs_serve_opts* o) {
         return nullptr;
     }
     s->opts = *o;
+    s->pair_wpb = std::max(2, o->warps_per_block);
     cudaGetDevice(&s->device);
-    const int nw = 2 * ((o->max_N + 63) / 64);
-    s->nwmax = nw;
-    s->pop_stride_words = static_cast<size_t>(o->max_K) * nw + static_cast<size_t>(o->max_K);
+    // the arena: hbm_budget_bytes, or room for max_slots requests of (max_N, max_K)
+    labs_request biggest{};
+    biggest.N = o->max_N;
+    biggest.K = o->max_K;
+    const int64_t fp_max = footprint(biggest);
+    const int64_t arena_bytes = o->hbm_budget_bytes > 0 ? (o->hbm_budget_bytes & ~int64_t{15})
+                                                        : fp_max * static_cast<int64_t>(o->max_slots);
+    if (arena_bytes < fp_max) {
+        fail(LABS_EINVAL, "hbm_budget_bytes=%lld holds no request of max_N=%d, max_K=%d (%lld bytes)",
+             static_cast<long long>(o->hbm_budget_bytes), o->max_N, o->max_K, static_cast<long long>(fp_max));
+        delete s;
+        return nullptr;
+    }
+    s->arena.init(arena_bytes);
+    s->stats.arena_bytes = arena_bytes;
     const size_t S = static_cast<size_t>(o->max_slots);
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    // one wave per class: warps of its kernel resident at once with its shared memory
+    for (int c = 0; c <= top && e == cudaSuccess; ++c) {
+        s->cls_smem[c] = lgpu::serve_smem_per_warp(kClassNw[c], o->max_K);
+        int blocks = 0;
+        e = lgpu::serve_blocks_per_sm(kClassNw[c], 1, o->warps_per_block, s->cls_smem[c], &blocks);
+        if (e == cudaSuccess && blocks < 1) {
+            fail(LABS_EINVAL, "the quantum kernel for %d-word sequences does not fit on an SM", kClassNw[c]);
+            free_server(s);
+            return nullptr;
+        }
+        s->cls_cap[c] = static_cast<int64_t>(blocks) * o->warps_per_block * sm_count();
+        if (e == cudaSuccess && o->warps_per_request == 2 && lgpu::serve_pairs_supported(kClassNw[c])) {
+            int b2 = 0;
+            e = lgpu::serve_blocks_per_sm(kClassNw[c], 2, s->pair_wpb, s->cls_smem[c], &b2);
+            s->cls_cap2[c] = static_cast<int64_t>(b2) * s->pair_wpb * sm_count();
+        }
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cls_stream[c], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join[c], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = cudaEventCreate(&s->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&s->ev1);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->d_off), sizeof(int64_t) * S);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&s->h_off), sizeof(int64_t) * S);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->d_cfg), sizeof(labs_instance) * S);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->d_state), sizeof(lgpu::ServeState) * S);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->d_pop), sizeof(uint32_t) * s->pop_stride_words * S);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->d_pop), static_cast<size_t>(arena_bytes));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->d_active), sizeof(int32_t) * S);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->d_out), sizeof(labs_device_result) * S);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->d_done), sizeof(int32_t) * S);

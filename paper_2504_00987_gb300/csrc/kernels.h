@@ -90,8 +90,8 @@ struct ServeState {
 struct ServeArgs {
     const labs_instance* cfg;    // per slot
     ServeState* state;           // per slot
-    uint32_t* pop;               // per-slot arena: K*NW words then K energies
-    size_t pop_stride_words;
+    uint32_t* pop;               // arena: a slot's extent holds K*NW words then K energies
+    const int64_t* pop_off;      // per slot: word offset of its extent in the arena
     const int32_t* active;       // slot of each active index
     int32_t n_active;
     int64_t quantum_steps;       // a slot stops at the first generation boundary past this
@@ -104,9 +104,19 @@ struct ServeArgs {
 
 size_t mts_smem_per_warp(int N, int K);
 cudaError_t launch_skew(const uint64_t* d_seqs, int N, int64_t B, int32_t* d_out, cudaStream_t stream);
-cudaError_t launch_serve_quantum(const ServeArgs& a, int nwmax, int warps_per_block, cudaStream_t stream);
-cudaError_t batch_prepare(int nwmax, int warps_per_block, size_t smem_per_warp, int* max_blocks_per_sm);
-cudaError_t launch_batch(const BatchArgs& a, int nwmax, int blocks, int warps_per_block,
+// Word count the service's kernels use for N, and one warp's shared memory for (nw, K).
+int serve_class_nw(int N);
+size_t serve_smem_per_warp(int nw, int K);
+// Resident CTAs per SM of the class-nw quantum kernel with wps warps per slot
+// (occupancy API); pairs exist for even nw only (serve_pairs_supported).
+int serve_pairs_supported(int nw);
+cudaError_t serve_blocks_per_sm(int nw, int wps, int warps_per_block, size_t smem_per_warp, int* blocks);
+// One quantum of the slots of one word-count class, wps warps per slot (an
+// even warps_per_block for wps = 2).
+cudaError_t launch_serve_quantum(const ServeArgs& a, int nw, int wps, int warps_per_block, cudaStream_t stream);
+// wps: warps per replica (1, or 2 with an even warps_per_block).
+cudaError_t batch_prepare(int nwmax, int wps, int warps_per_block, size_t smem_per_warp, int* max_blocks_per_sm);
+cudaError_t launch_batch(const BatchArgs& a, int nwmax, int wps, int blocks, int warps_per_block,
                          cudaStream_t stream);
 cudaError_t launch_mts(const MtsArgs& a, cudaStream_t stream);
 cudaError_t launch_tabu(const TabuArgs& a, cudaStream_t stream);

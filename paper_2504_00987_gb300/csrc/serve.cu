@@ -1,15 +1,17 @@
 // serve.cu -- the quantum kernel of the solve service.  Every active slot
 // (one admitted request) gets one warp: the warp resumes the slot's replica
-// from its device-resident state (population and energies in the HBM
-// arena, best sequence and counters in the slot record), runs whole
-// generations until the replica stops or the quantum's step allowance is
-// used, and suspends it again.  Suspension only ever happens at a
-// generation boundary, where the replica's state is exactly (population,
-// best, g, steps), so a request's trajectory does not depend on the quantum
-// size or on which other requests share the launch.  The kernel never waits
-// on anything: it is bounded by the quantum and one generation.  The quantum
-// is a step count, and optionally a device-time budget, so that slots of
-// small N are not held to the pace of the largest one.
+// from its device-resident state (population and energies in the slot's
+// extent of the HBM arena, best sequence and counters in the slot record),
+// runs whole generations until the replica stops or the quantum's step
+// allowance is used, and suspends it again.  Suspension only ever happens
+// at a generation boundary, where the replica's state is exactly
+// (population, best, g, steps), so a request's trajectory does not depend
+// on the quantum size or on which other requests share the launch.  The
+// kernel never waits on anything: it is bounded by the quantum and one
+// generation.  The quantum is a step count, and optionally a device-time
+// budget, so that slots of small N are not held to the pace of the largest
+// one.  One launch serves one word-count class (serve_class_nw), so its
+// shared memory per warp is that class's, not the largest N's.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -42,17 +44,23 @@ __device__ __forceinline__ uint64_t warp_globaltimer(int lane) {
     return __shfl_sync(kFull, t, 0);
 }
 
-template <int NW>
+// One slot's quantum.  WPS = 2: two warps run the slot's replica (each on its
+// own copy of the state, splitting every tabu step's neighbours); the lower
+// one takes the device-time decisions and writes the state back, and the
+// pair shakes hands after loading so that the write-back cannot overtake the
+// other warp's load.
+template <int NW, int WPS, int HALF>
 __device__ void serve_slot(const ServeArgs& a, int i, int slot, const labs_instance& in,
-                           unsigned char* base, int lane) {
+                           unsigned char* base, int lane, PairLink* link) {
     const ReplicaCfg cfg = serve_cfg(in);
     const int K = cfg.K;
     uint32_t* pop = reinterpret_cast<uint32_t*>(base);
     int32_t* popE = reinterpret_cast<int32_t*>(pop + K * NW);
     int32_t* Cs = popE + K;
-    uint32_t* hpop = a.pop + static_cast<size_t>(slot) * a.pop_stride_words;
+    uint32_t* hpop = a.pop + a.pop_off[slot];
     int32_t* hpopE = reinterpret_cast<int32_t*>(hpop + K * NW);
     ServeState* S = a.state + slot;
+    uint32_t xseq = 1;
 
     ReplicaState<NW> st;
     if (S->phase == kSlotFresh) {
@@ -68,6 +76,10 @@ __device__ void serve_slot(const ServeArgs& a, int i, int slot, const labs_insta
         st.steps = S->steps;
         __syncwarp();
     }
+    if constexpr (WPS == 2) {
+        uint64_t o = 0;
+        if (!pair_exchange(link, HALF, xseq++, 0u, o, lane)) st.status = LABS_RUN_SYNC_LOST;
+    }
     int64_t used = 0, trace_len = 0;
     bool finished = false;
     const uint64_t t0 = a.quantum_ns ? warp_globaltimer(lane) : 0;
@@ -77,9 +89,22 @@ __device__ void serve_slot(const ServeArgs& a, int i, int slot, const labs_insta
             break;
         }
         if (used >= a.quantum_steps) break;
-        if (a.quantum_ns && gens > 0 && warp_globaltimer(lane) - t0 >= a.quantum_ns) break;
-        used += replica_generation<NW>(cfg, st, pop, popE, Cs, nullptr, 0, trace_len, nullptr, lane);
+        if (a.quantum_ns && gens > 0) {
+            bool over = HALF == 0 && warp_globaltimer(lane) - t0 >= a.quantum_ns;
+            if constexpr (WPS == 2) {  // the lower warp's clock decides for both
+                uint64_t o = 0;
+                if (!pair_exchange(link, HALF, xseq++, over ? 1u : 0u, o, lane)) {
+                    st.status = LABS_RUN_SYNC_LOST;
+                    continue;  // stops at the test above
+                }
+                over = o != 0 || (HALF == 0 && over);
+            }
+            if (over) break;
+        }
+        used += replica_generation<NW, false, false, WPS, HALF>(cfg, st, pop, popE, Cs, nullptr, 0, trace_len,
+                                                                nullptr, lane, link, &xseq);
     }
+    if (HALF != 0) return;
     if (finished) {
         replica_store_result<NW>(st, 0, a.out + i, lane);
     } else {
@@ -103,58 +128,85 @@ __device__ void serve_slot(const ServeArgs& a, int i, int slot, const labs_insta
     }
 }
 
-template <int NWMAX>
-__global__ void __launch_bounds__(256) serve_quantum_kernel(const ServeArgs a) {
+// Pairs take as many registers as they need (at most one CTA per SM is
+// promised, which spares them spills); single warps keep the default budget.
+template <int NW, int WPS>
+__global__ void __launch_bounds__(256, WPS == 2 ? 1 : 0) serve_quantum_kernel(const ServeArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PairLink links[8 / WPS];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * (blockDim.x >> 5) + warp;
+    PairLink* link = &links[warp / WPS];
+    if constexpr (WPS == 2) {
+        if (lane < 4) reinterpret_cast<unsigned long long*>(link->slot)[lane] = 0ull;
+        __syncthreads();  // every link word is zero before either warp of a pair publishes
+    }
+    const int i = (blockIdx.x * (blockDim.x >> 5) + warp) / WPS;
     if (i >= a.n_active) return;
     unsigned char* base = smem + static_cast<size_t>(warp) * a.smem_per_warp;
     const int slot = a.active[i];
     const labs_instance in = a.cfg[slot];
-    const int W = (in.N + 63) / 64;
-    if (W == 1) {
-        serve_slot<2>(a, i, slot, in, base, lane);
-    } else if (W == 2) {  // three 32-bit words up to N = 96
-        if constexpr (NWMAX >= 4) {
-            if (in.N <= 96)
-                serve_slot<3>(a, i, slot, in, base, lane);
-            else
-                serve_slot<4>(a, i, slot, in, base, lane);
+    if (WPS == 2 && (warp & 1))
+        serve_slot<NW, WPS, WPS - 1>(a, i, slot, in, base, lane, link);
+    else
+        serve_slot<NW, WPS, 0>(a, i, slot, in, base, lane, link);
+}
+
+int serve_class_nw(int N) { return N <= 64 ? 2 : N <= 96 ? 3 : N <= 128 ? 4 : N <= 160 ? 5 : N <= 192 ? 6 : 8; }
+
+size_t serve_smem_per_warp(int nw, int K) {
+    // population (K x nw words), energies (K), two buffers of C_k (64 nw)
+    const size_t bytes = (static_cast<size_t>(K) * nw + static_cast<size_t>(K) + 64u * nw) * 4u;
+    return (bytes + 15) & ~static_cast<size_t>(15);
+}
+
+// Two warps per slot need an even word count (the halves of every step).
+static const void* serve_fn(int nw, int wps) {
+    if (wps == 2) {
+        switch (nw) {
+            case 2: return reinterpret_cast<const void*>(&serve_quantum_kernel<2, 2>);
+            case 4: return reinterpret_cast<const void*>(&serve_quantum_kernel<4, 2>);
+            case 6: return reinterpret_cast<const void*>(&serve_quantum_kernel<6, 2>);
+            case 8: return reinterpret_cast<const void*>(&serve_quantum_kernel<8, 2>);
+            default: break;
         }
-    } else if (W == 3) {  // five 32-bit words up to N = 160
-        if constexpr (NWMAX >= 6) {
-            if (in.N <= 160)
-                serve_slot<5>(a, i, slot, in, base, lane);
-            else
-                serve_slot<6>(a, i, slot, in, base, lane);
-        }
-    } else {
-        if constexpr (NWMAX >= 8) serve_slot<8>(a, i, slot, in, base, lane);
+    }
+    switch (nw) {
+        case 2: return reinterpret_cast<const void*>(&serve_quantum_kernel<2, 1>);
+        case 3: return reinterpret_cast<const void*>(&serve_quantum_kernel<3, 1>);
+        case 4: return reinterpret_cast<const void*>(&serve_quantum_kernel<4, 1>);
+        case 5: return reinterpret_cast<const void*>(&serve_quantum_kernel<5, 1>);
+        case 6: return reinterpret_cast<const void*>(&serve_quantum_kernel<6, 1>);
+        default: return reinterpret_cast<const void*>(&serve_quantum_kernel<8, 1>);
     }
 }
 
-cudaError_t launch_serve_quantum(const ServeArgs& a, int nwmax, int warps_per_block, cudaStream_t stream) {
-    if (a.n_active <= 0) return cudaSuccess;
-    const size_t smem = a.smem_per_warp * warps_per_block;
-    const int blocks = (a.n_active + warps_per_block - 1) / warps_per_block;
-    const void* fn;
-    switch (nwmax) {
-        case 2: fn = reinterpret_cast<const void*>(&serve_quantum_kernel<2>); break;
-        case 4: fn = reinterpret_cast<const void*>(&serve_quantum_kernel<4>); break;
-        case 6: fn = reinterpret_cast<const void*>(&serve_quantum_kernel<6>); break;
-        default: fn = reinterpret_cast<const void*>(&serve_quantum_kernel<8>); break;
-    }
+int serve_pairs_supported(int nw) { return nw % 2 == 0 ? 1 : 0; }
+
+cudaError_t serve_blocks_per_sm(int nw, int wps, int warps_per_block, size_t smem_per_warp, int* blocks) {
+    const void* fn = serve_fn(nw, wps);
+    const size_t smem = smem_per_warp * warps_per_block;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    switch (nwmax) {
-        case 2: serve_quantum_kernel<2><<<blocks, warps_per_block * 32, smem, stream>>>(a); break;
-        case 4: serve_quantum_kernel<4><<<blocks, warps_per_block * 32, smem, stream>>>(a); break;
-        case 6: serve_quantum_kernel<6><<<blocks, warps_per_block * 32, smem, stream>>>(a); break;
-        default: serve_quantum_kernel<8><<<blocks, warps_per_block * 32, smem, stream>>>(a); break;
-    }
-    return cudaGetLastError();
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, warps_per_block * 32, smem);
+}
+
+cudaError_t launch_serve_quantum(const ServeArgs& a, int nw, int wps, int warps_per_block, cudaStream_t stream) {
+    if (a.n_active <= 0) return cudaSuccess;
+    if (wps == 2 && (nw % 2 != 0 || warps_per_block % 2 != 0)) return cudaErrorInvalidValue;
+    const size_t smem = a.smem_per_warp * warps_per_block;
+    const int slots_per_block = warps_per_block / wps;
+    const int blocks = (a.n_active + slots_per_block - 1) / slots_per_block;
+    const void* fn = serve_fn(nw, wps);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(blocks));
+    cfg.blockDim = dim3(static_cast<unsigned>(warps_per_block * 32));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    void* args[] = {const_cast<ServeArgs*>(&a)};
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 }  // namespace lgpu

@@ -137,6 +137,9 @@ def test_batch_argument_errors_without_gpu(lib):
     bad_map = nat.Mapping(3, 1, 0, 0)
     arr[1].max_steps = 10
     assert lib.labs_batch_create(arr, 2, ctypes.byref(bad_map), None, ctypes.byref(h)) == nat.LABS_EINVAL
+    for bad_map in (nat.Mapping(1, 1, 0, 2), nat.Mapping(4, 1, 0, 3)):  # a pair needs 2+ warps; 1 or 2
+        assert lib.labs_batch_create(arr, 2, ctypes.byref(bad_map), None, ctypes.byref(h)) == nat.LABS_EINVAL
+        assert b"warps_per_seq" in lib.labs_last_error()
     assert lib.labs_batch_destroy(None) == nat.LABS_OK
 
 
@@ -151,7 +154,10 @@ def test_serve_argument_errors_without_gpu(lib):
     bad = nat.ServeOpts(16, 64, 100, 4, 1000, 10, 0, 0, -5)  # negative time budget
     assert not lib.labs_serve_create(ctypes.byref(bad))
     assert b"quantum_us" in lib.labs_last_error()
-    assert ctypes.sizeof(nat.ServeOpts) == 4 * 4 + 8 * 5
+    bad = nat.ServeOpts(16, 64, 100, 4, 1000, 10, 0, 0, 0, 3, 0)  # warps_per_request 3
+    assert not lib.labs_serve_create(ctypes.byref(bad))
+    assert b"warps_per_request" in lib.labs_last_error()
+    assert ctypes.sizeof(nat.ServeOpts) == 4 * 4 + 8 * 5 + 4 * 2
     assert lib.labs_serve_destroy(None) == nat.LABS_OK
     assert lib.labs_serve_poll(None, 1, None) == nat.LABS_EINVAL
 

@@ -57,11 +57,18 @@ def test_uneven_512_equals_oracle(labs, orc):
         got = b.results()
         mapping = b.mapping
     assert mapping["warps_per_block"] in (1, 2, 4, 8) and mapping["blocks_per_sm"] >= 1
+    assert mapping["warps_per_seq"] in (1, 2)
     ora = oracle_results(orc, wl_list)
     for g, o, x in zip(got, ora, wl_list):
         assert g["N"] == x.N and g["instance"] == x.instance
         assert_same(g, o)
         assert g["steps"] == x.max_steps
+    # the same 512 on two warps per replica (whichever mapping the tuner chose)
+    other = 2 if mapping["warps_per_seq"] == 1 else 1
+    got2 = labs.mts_batch_run(inst, mapping={"warps_per_block": 4, "blocks_per_sm": 2, "order": 0,
+                                             "warps_per_seq": other})
+    for g, o in zip(got2, ora):
+        assert_same(g, o)
 
 
 def test_mapping_and_order_do_not_change_results(labs):
@@ -72,10 +79,14 @@ def test_mapping_and_order_do_not_change_results(labs):
     ref = labs.mts_batch_run(inst, mapping={"warps_per_block": 4, "blocks_per_sm": 1, "order": 0})
     for m in ({"warps_per_block": 1, "blocks_per_sm": 1, "order": 1},
               {"warps_per_block": 8, "blocks_per_sm": 2, "order": 0},
-              {"warps_per_block": 2, "blocks_per_sm": 4, "order": 1}):
+              {"warps_per_block": 2, "blocks_per_sm": 4, "order": 1},
+              {"warps_per_block": 2, "blocks_per_sm": 1, "order": 0, "warps_per_seq": 2},
+              {"warps_per_block": 4, "blocks_per_sm": 3, "order": 1, "warps_per_seq": 2},
+              {"warps_per_block": 8, "blocks_per_sm": 1, "order": 0, "warps_per_seq": 2}):
         got = labs.mts_batch_run(inst, mapping=m)
         for a, b in zip(ref, got):
             assert a["E"] == b["E"] and a["seq"] == b["seq"] and a["steps"] == b["steps"]
+            assert a["status"] == b["status"] == labs.RUN_BUDGET
 
 
 def test_relaunch_and_single_instance_equivalence(labs):
@@ -95,15 +106,49 @@ def test_relaunch_and_single_instance_equivalence(labs):
         assert alone["E"] == first[i]["E"] and alone["seq"] == first[i]["seq"]
 
 
-def test_mixed_widths_up_to_256(labs, orc):
+@pytest.mark.parametrize("wps", [1, 2])
+def test_mixed_widths_up_to_256(labs, orc, wps):
     wl = []
     from paper_2504_00987_gb300.workloads import Instance
 
     for i, (N, K) in enumerate([(3, 2), (64, 10), (65, 10), (128, 8), (129, 6), (192, 5), (193, 4), (256, 3)]):
         wl.append(Instance(N, K, 5, 100 + i, 600))
-    got = labs.mts_batch_run(to_instances(labs, wl))
+    got = labs.mts_batch_run(to_instances(labs, wl), mapping={"warps_per_block": 2, "blocks_per_sm": 1,
+                                                              "order": 0, "warps_per_seq": wps})
     for g, o in zip(got, oracle_results(orc, wl)):
         assert_same(g, o)
+
+
+def test_two_warps_per_replica_with_targets_variants_and_ties(labs, orc):
+    """Two warps per replica on the decisions that cross the pair: targets
+    (the replica stops mid-run), s_1 = +1 (bit 0 never moves, in the lower
+    half), replace-worst, small N where ties for the minimum are frequent,
+    and every word count."""
+    from paper_2504_00987_gb300.workloads import Instance
+
+    wl = [Instance(N, K, 8, i, 3000, target_E=t) for i, (N, K, t) in
+          enumerate([(5, 3, -1), (9, 4, -1), (13, 10, 14), (40, 20, 108), (70, 12, -1), (100, 30, -1),
+                     (150, 8, -1), (200, 5, -1), (256, 4, -1)])]
+    inst = to_instances(labs, wl)
+    m2 = {"warps_per_block": 4, "blocks_per_sm": 1, "order": 0, "warps_per_seq": 2}
+    for g, o in zip(labs.mts_batch_run(inst, mapping=m2), oracle_results(orc, wl)):
+        assert_same(g, o)
+    for variant, policy in ((2, 0), (1, 1), (3, 1)):
+        inst = [labs.make_instance(x.N, x.K, seed=8, instance=x.instance, max_steps=3000, variant=variant,
+                                   replace_policy=policy) for x in wl]
+        got = labs.mts_batch_run(inst, mapping=m2)
+        for g, x in zip(got, wl):
+            o, _, _ = orc.mts_run(orc.make_params(x.N, x.K, max_steps=3000, variant=variant,
+                                                  replace_policy=policy), 8, x.instance)
+            assert_same(g, o)
+
+
+def test_mapping_errors(labs):
+    inst = [labs.make_instance(40, 10, max_steps=100)]
+    for bad in ({"warps_per_block": 1, "blocks_per_sm": 1, "warps_per_seq": 2},
+                {"warps_per_block": 4, "blocks_per_sm": 1, "warps_per_seq": 3}):
+        with pytest.raises(labs.LabsError):
+            labs.mts_batch_run(inst, mapping=bad)
 
 
 def test_batch_with_targets_and_generation_budgets(labs, orc):

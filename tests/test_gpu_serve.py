@@ -173,3 +173,64 @@ def test_quantum_timeout_fails_the_server_cleanly(labs):
     # the device is still usable afterwards
     P = labs.make_params(40, 10, max_steps=100)
     assert labs.mts_run(P, 0, 0, 2)[0]["steps"] == 100
+
+
+def test_admission_waits_for_arena_memory(labs):
+    """A request waits for arena memory, not for a slot: the arena holds one
+    N = 64, K = 100 population (K (nw + 1) 4 = 1,200 bytes, nw = 2) and there
+    are 8 slots, so the three requests run one after another; each result is
+    its run alone."""
+    reqs = [labs.make_instance(64, 100, seed=9, instance=i, max_steps=3000) for i in range(3)]
+    with labs.Server(max_slots=8, max_N=64, max_K=100, quantum_steps=200, hbm_budget_bytes=1216) as srv:
+        res = wait_all(srv, [srv.submit(r) for r in reqs])
+        st = srv.stats()
+    assert st["completed"] == 3 and st["failed"] == 0
+    assert st["deferred_hbm"] >= 1 and st["deferred_slots"] == 0 and st["deferred_smem"] == 0
+    assert st["arena_bytes"] == 1216 and st["arena_used_bytes"] == 0
+    for r, g in zip(reqs, res):
+        assert same(g, alone(labs, r))
+
+
+def test_arena_smaller_than_one_request_is_refused(labs):
+    with pytest.raises(labs.LabsError):
+        labs.Server(max_slots=8, max_N=64, max_K=100, hbm_budget_bytes=1000)
+
+
+def test_admission_waits_for_shared_memory(labs):
+    """With populations of up to K = 1024, the 256-bit class's quantum kernel
+    keeps few warps resident per SM; requests beyond one resident wave wait in
+    the queue (held by shared memory, not by slots or arena) and all finish
+    with their results alone.  A 64-bit request shares the wave by fraction."""
+    reqs = [labs.make_instance(256, 2, seed=5, instance=i, max_steps=3000) for i in range(1500)]
+    reqs.append(labs.make_instance(64, 50, seed=5, instance=9999, max_steps=5000))
+    with labs.Server(max_slots=4096, max_N=256, max_K=1024, quantum_steps=500) as srv:
+        res = wait_all(srv, [srv.submit(r) for r in reqs], timeout=300.0)
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["deferred_smem"] >= 1 and st["deferred_slots"] == 0 and st["deferred_hbm"] == 0
+    for r, g in list(zip(reqs, res))[::97] + [(reqs[-1], res[-1])]:
+        assert same(g, alone(labs, r))
+
+
+def test_warp_pairs_do_not_change_results(labs, orc):
+    """Quanta that run requests on two warps (warps_per_request = 2, taken
+    whenever the active requests fit one resident wave that way) give the
+    results of one warp per request, of the run alone and of the oracle --
+    with device-time quanta, so the pair's shared suspension decision is
+    exercised too."""
+    reqs = random_requests(labs, 60, seed=45, max_n=256, steps=(500, 12_000))
+    outs, stats = [], []
+    for wpr, kw in ((1, dict(quantum_steps=700)), (2, dict(quantum_steps=700)),
+                    (2, dict(quantum_steps=1 << 40, quantum_us=400))):
+        with labs.Server(max_slots=24, max_N=256, max_K=100, warps_per_request=wpr, **kw) as srv:
+            outs.append(wait_all(srv, [srv.submit(r) for r in reqs]))
+            stats.append(srv.stats())
+    assert stats[0]["pair_quanta"] == 0 and stats[1]["pair_quanta"] > 0 and stats[2]["pair_quanta"] > 0
+    for st in stats:
+        assert st["completed"] == 60 and st["failed"] == 0
+    for a, b, c in zip(*outs):
+        assert same(a, b) and same(a, c) and a["status"] == labs.RUN_BUDGET
+    for r, g in list(zip(reqs, outs[1]))[::12]:
+        assert same(g, alone(labs, r))
+        o, _, _ = orc.mts_run(orc.make_params(r.N, r.K, max_steps=r.max_steps), r.seed, r.instance)
+        assert g["E"] == o["E"] and g["seq"] == [int(x) for x in o["seq"]]
