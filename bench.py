@@ -332,7 +332,7 @@ def c2_extras(args, torch, labs, pg, dev, world, rank, stream) -> dict:
     first, _ = parallel.shard(world, rank, reps)
     rows = sweep_rows(torch, labs, pg, dev, first, reps, steps, 1, 1, stream, world)
     targets = load_targets("sweep_n92_120")
-    treps, cap = sms * 8, 10_000_000
+    treps, cap = sms * TTS_REPLICAS_PER_SM, 10_000_000
     trows = tts_rows(torch, labs, SWEEP_NS, targets, treps, cap, args.tts_runs, stream, pg=pg, rank=rank)
     return {
         "sweep_n92_120": {"workload": f"N=92..120 step 4, K=100, {reps} replicas x {steps} tabu steps per N "
@@ -479,6 +479,12 @@ def fit_exponential(Ns, medians):
             "N_min_fit": int(min(Ns)), "N_max_fit": int(max(Ns))}
 
 
+# Time to target runs 16 replicas per SM: measured against 8, 4 and 32 per SM on
+# the N = 92..120 targets, 16 gave the lowest median p50 (3.0 ms against 3.3 ms at 8;
+# 32 per SM cannot all be resident, so the flag stops the first wave's search).
+TTS_REPLICAS_PER_SM = 16
+
+
 def tts_run_ranks(torch, labs, pg, dev, n, target, seed, first, reps, cap, state, out, flag, stream,
                   slice_gens=100):
     """One time-to-target run on every rank: the rank's replicas advance in slices
@@ -584,7 +590,7 @@ def run_tts(args) -> None:
     kind = "optimum_n16_36" if args.tts_targets == "optimum" else "sweep_n92_120"
     targets = load_targets(kind)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    reps = args.replicas or sms * 8
+    reps = args.replicas or sms * TTS_REPLICAS_PER_SM
     cap = args.steps_per_replica or 10_000_000
     stream = torch.cuda.current_stream()
     Ns = [int(x) for x in args.tts_n.split(",")] if args.tts_n else sorted(targets)
@@ -727,7 +733,11 @@ def run_batch(args) -> None:
     flips = sum(x.max_steps * x.N for x in wl)
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    mapping = labs.autotune(inst)
+    if args.batch_mapping:  # profiling: this mapping only (no tuning, grid or plain form)
+        wpb, bps, wps = (int(v) for v in args.batch_mapping.split(","))
+        mapping = {"warps_per_block": wpb, "blocks_per_sm": bps, "order": 0, "warps_per_seq": wps}
+    else:
+        mapping = labs.autotune(inst)
     tune_s = time.perf_counter() - t0
     def makespan(m, steps):
         with labs.Batch(inst, mapping=m) as b:
@@ -738,6 +748,14 @@ def run_batch(args) -> None:
 
     ms = parallel.max_over_ranks(pg, [makespan(mapping, args.steps)], dev)[0]
     total_flips = parallel.sum_over_ranks(pg, [float(flips)], dev)[0]
+    if args.batch_mapping:
+        if rank == 0:
+            print(json.dumps({"metric": "flip-evals/s", "value": total_flips / (ms / 1e3), "unit": "flip-evals/s",
+                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                              "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+                              "config": {"workload": "batch_uneven_512 (profiling: fixed mapping)",
+                                         "mapping": mapping}}), flush=True)
+        return
     # other mappings, for the record: one and two warps per replica
     grid = []
     for wps in (1, 2):
@@ -943,6 +961,8 @@ def main() -> None:
     ap.add_argument("--baseline-requests", type=int, default=400, help="serve: plain-form prefix")
     ap.add_argument("--slots", type=int, default=0, help="serve: resident slots")
     ap.add_argument("--quantum-steps", type=int, default=2000, help="serve: tabu steps per slot per quantum")
+    ap.add_argument("--batch-mapping", default="",
+                    help="batch, profiling only: 'warps_per_block,blocks_per_sm,warps_per_seq', one mapping")
     ap.add_argument("--warps-per-request", type=int, default=1,
                     help="serve: 1 = one warp per request, 2 = warp pairs while they fit")
     ap.add_argument("--quantum-us", type=int, default=4000,

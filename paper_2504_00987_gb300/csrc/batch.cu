@@ -56,7 +56,19 @@ __device__ __forceinline__ void batch_unit(const BatchArgs& a, unsigned char* ba
         }
         if constexpr (WPS == 2) {
             uint64_t o = 0;
-            if (!pair_exchange(link, HALF, xseq++, HALF == 0 ? idx : 0u, o, lane)) break;
+            if (!pair_exchange(link, HALF, xseq++, HALF == 0 ? idx : 0u, o, lane)) {
+                // the pair lost step: the instance this warp took is reported, not run
+                if (HALF == 0 && lane == 0 && idx < static_cast<unsigned long long>(a.n)) {
+                    labs_device_result* out = a.out + a.order[idx];
+                    for (int w = 0; w < LABS_MAX_W; ++w) out->seq[w] = 0;
+                    out->E = -1;
+                    out->status = LABS_RUN_SYNC_LOST;
+                    out->generations = 0;
+                    out->steps = 0;
+                    out->trace_len = 0;
+                }
+                break;
+            }
             if (HALF == 1) idx = o;
         }
         if (idx >= static_cast<unsigned long long>(a.n)) break;
@@ -84,7 +96,7 @@ __device__ __forceinline__ void batch_unit(const BatchArgs& a, unsigned char* ba
 template <int NWMAX, int WPS>
 __global__ void __launch_bounds__(256, WPS == 2 ? 1 : 0) batch_kernel(const BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ PairLink links[8 / WPS];
+    __shared__ PairLink links[WPS == 2 ? 4 : 1];  // one per pair of an 8-warp CTA
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     unsigned char* base = smem + static_cast<size_t>(warp) * a.smem_per_warp;

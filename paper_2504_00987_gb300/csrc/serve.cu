@@ -133,10 +133,10 @@ __device__ void serve_slot(const ServeArgs& a, int i, int slot, const labs_insta
 template <int NW, int WPS>
 __global__ void __launch_bounds__(256, WPS == 2 ? 1 : 0) serve_quantum_kernel(const ServeArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ PairLink links[8 / WPS];
+    __shared__ PairLink links[WPS == 2 ? 4 : 1];  // one per pair of an 8-warp CTA
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    PairLink* link = &links[warp / WPS];
+    PairLink* link = WPS == 2 ? &links[warp >> 1] : nullptr;
     if constexpr (WPS == 2) {
         if (lane < 4) reinterpret_cast<unsigned long long*>(link->slot)[lane] = 0ull;
         __syncthreads();  // every link word is zero before either warp of a pair publishes
