@@ -24,6 +24,7 @@ import ctypes
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -46,10 +47,16 @@ KERNEL_SOURCES = ["tabu_core.cuh", "tabu_skew.cuh", "replica.cuh", "mts_kernels.
 
 
 def kernel_hash() -> str:
+    """Hash of the code the MTS kernel is compiled from: comments and blank
+    space are left out, so that an edit of a comment does not orphan the
+    recorded DRAM traffic of an unchanged kernel."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2504_00987_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2504_00987_gb300", "csrc", f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)  # block comments
+        text = re.sub(r"//[^\n]*", " ", text)                # line comments
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

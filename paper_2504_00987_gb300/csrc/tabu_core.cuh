@@ -1,26 +1,29 @@
 // tabu_core.cuh -- one warp runs one tabu search (Algorithm 2 / Algorithm 4).
 //
-// Neighbour scoring (Sec. III.C).  Flipping s_j changes C_k by
+// Neighbour scoring (Sec. III.C, Table I).  Flipping s_j changes C_k by
 // delta_k(j) = -2 s_j (s_{j+k} + s_{j-k}) (terms outside 1..N dropped), so
 //   E_j = E + sum_k delta_k (2 C_k + delta_k)
-//       = E + 4(N-1) + 8 M_j - 4 s_j (2 S_j - T_j),
-// with (0-based bits b_i, s_i = 2 b_i - 1)
-//   M_j = sum_{k=1}^{min(j, N-1-j)} s_{j+k} s_{j-k},
-//   S_j = sum_k C_k (b_{j+k} + b_{j-k}),
-//   T_j = sum_{k<=j} C_k + sum_{k<=N-1-j} C_k.
-// S_j is evaluated on bit planes: with C_k in P-bit two's complement
-// (P = bit length of max|C_k| plus a sign bit), S_j = sum_m w_m
-// [popc(t_m & X_j) + popc(t_m & Y_j)], where t_m is the bit vector over k of
-// bit m of C_k (from a warp ballot), w_m = 2^m (-2^(P-1) for the sign
-// plane), X_j = pivot >> j (bit k = b_{j+k}) and Y_j the mirrored window
-// (bit k = b_{j-k}).  Every popcount covers 32 pair-terms of one plane, and
-// the arithmetic is exact int32 throughout.
+//       = E + 4(N-1) + 8 M_j - 4 s_j R_j,
+// with M_j = sum_{k>=1} s_{j+k} s_{j-k} (a masked popcount of the XOR of the
+// two windows of j) and R_j = sum_k C_k (s_{j+k} + s_{j-k}).  R_j is set up
+// once per search on bit planes (0-based bits b_i, s_i = 2 b_i - 1):
+//   R_j = 2 S_j - T_j,  S_j = sum_k C_k (b_{j+k} + b_{j-k}),
+//   T_j = sum_{k<=j} C_k + sum_{k<=N-1-j} C_k,
+// where S_j = sum_m w_m [popc(t_m & X_j) + popc(t_m & Y_j)] over the
+// two's-complement planes t_m of C_k (from warp ballots), X_j = pivot >> j
+// (bit k = b_{j+k}) and Y_j the mirrored window (bit k = b_{j-k}); T_j comes
+// from prefix sums of C_k.  After every move R_j is updated exactly instead
+// of re-scored (the identity is derived above tabu_search), so a step costs
+// about one bit plane of the from-scratch scoring.  Arithmetic is exact int32.
 //
-// Work split: lane l scores neighbours j = l + 32q; lane l keeps C_k and the
-// tabu expiry of index l + 32q in registers.  The admissible minimum is a
-// warp redux; ties are counted with ballots and broken by the step's tie
-// draw in ascending j.  Applying the move updates C_k in O(N) (one delta
-// per lane slot), flips the pivot and sets the tenure.
+// Work split: lane l scores neighbours j = l + 32q and keeps their R_j and
+// tabu expiry in registers; C_k before and after the move sit in two
+// warp-private shared-memory buffers.  The admissible minimum is one
+// redux.sync.min over packed (E_j, j) keys, the ties are counted by one
+// redux.sync.add, and a tie pick by the step's draw in ascending j uses
+// ballots only when it is not the lowest minimiser.  Applying the move
+// flips the pivot, recomputes (short sequences) or updates C_k, updates
+// every R_j and sets the tenure.
 #pragma once
 
 #include <climits>

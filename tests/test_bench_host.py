@@ -50,3 +50,33 @@ def test_clock_summary_from_samples(bench, tmp_path):
     out = s.summary()
     assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
     assert out["reasons"] == ["sw_power_cap"]  # the other GPU's slowdown is not ours
+
+
+def test_kernel_hash_ignores_comments_not_code(bench, tmp_path, monkeypatch):
+    """The DRAM traffic record is keyed by this hash: a comment edit keeps
+    it, any change of code orphans it (the bench line then reports null)."""
+    import os
+    import shutil
+
+    src = os.path.join(bench.ROOT, "paper_2504_00987_gb300", "csrc")
+    dst = tmp_path / "paper_2504_00987_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for f in bench.KERNEL_SOURCES:
+        shutil.copy(os.path.join(src, f), dst / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    base = bench.kernel_hash()
+    core = dst / "tabu_core.cuh"
+    text = core.read_text()
+    core.write_text("// a new comment line\n" + text.replace("#pragma once", "/* block\n comment */ #pragma once", 1))
+    assert bench.kernel_hash() == base
+    core.write_text(text.replace("kRecompute = NW <= 4", "kRecompute = NW <= 3", 1))
+    assert bench.kernel_hash() != base
+
+
+def test_traffic_record_matches_the_kernel(bench):
+    """profiles/ holds the DRAM traffic of the current MTS kernel."""
+    import json
+
+    rec = json.load(open(bench.TRAFFIC_FILE))
+    assert rec["kernel_hash"] == bench.kernel_hash()
+    assert 0 < rec["bytes_per_launch"] < 1 << 20
