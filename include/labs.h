@@ -199,9 +199,11 @@ typedef struct labs_mapping {
     int32_t warps_per_seq;   /* warps per replica: 1 (or 0), or 2 (warps_per_block 2, 4
                                 or 8): the two warps of a replica split every tabu
                                 step's neighbours and meet once per step in shared
-                                memory, which halves the serial chain of a step's
-                                scoring; a lost step (a bounded wait that runs out)
-                                stops the replica with LABS_RUN_SYNC_LOST */
+                                memory, which halves a step's scoring but repeats the
+                                move's bookkeeping in both warps (on GB300 slower than
+                                one warp for N <= 160; the autotuner times both); a
+                                lost step (a bounded wait that runs out) stops the
+                                replica with LABS_RUN_SYNC_LOST */
 } labs_mapping;
 
 typedef struct labs_batch labs_batch; /* opaque */
