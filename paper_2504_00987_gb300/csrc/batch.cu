@@ -40,7 +40,8 @@ __device__ __forceinline__ void run_instance(const ReplicaCfg& cfg, unsigned cha
     uint32_t* pop = reinterpret_cast<uint32_t*>(base);
     int32_t* popE = reinterpret_cast<int32_t*>(pop + cfg.K * NW);
     int32_t* Cs = popE + cfg.K;
-    replica_run<NW, false, false, WPS, HALF>(cfg, pop, popE, Cs, nullptr, 0, nullptr, out, lane, link, xseq);
+    // correlations updated per k (PERK): the batch's warps run alone on their SM sub-partitions
+    replica_run<NW, false, false, WPS, HALF, true>(cfg, pop, popE, Cs, nullptr, 0, nullptr, out, lane, link, xseq);
 }
 
 // The queue loop of one unit.  WPS = 2: half 0 takes the instance and tells

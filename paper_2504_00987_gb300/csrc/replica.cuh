@@ -177,7 +177,7 @@ __device__ __forceinline__ bool replica_should_stop(const ReplicaCfg& a, Replica
 // its partner, with which it meets through `link` inside the tabu search.
 // The global termination flag is not supported there (glf must be null: the
 // two warps could read it at different times).
-template <int NW, bool TRACE = false, bool SKEW = false, int WPS = 1, int HALF = 0>
+template <int NW, bool TRACE = false, bool SKEW = false, int WPS = 1, int HALF = 0, bool PERK = false>
 __device__ int64_t replica_generation(const ReplicaCfg& a, ReplicaState<NW>& st,
                                       uint32_t* __restrict__ pop, int32_t* __restrict__ popE,
                                       int32_t* __restrict__ Cs, int4* __restrict__ trace,
@@ -238,10 +238,10 @@ __device__ int64_t replica_generation(const ReplicaCfg& a, ReplicaState<NW>& st,
                                                       trace, trace_cap, trace_len, lane);
     } else {
         to = (a.variant & LABS_VARIANT_FIX_FIRST_SPIN)
-                 ? tabu_search<NW, TRACE, true, WPS, HALF>(child, N, a.key, a.inst, gg, max_iter, budget, Cs,
-                                                           trace, trace_cap, trace_len, lane, link, xseq)
-                 : tabu_search<NW, TRACE, false, WPS, HALF>(child, N, a.key, a.inst, gg, max_iter, budget, Cs,
-                                                            trace, trace_cap, trace_len, lane, link, xseq);
+                 ? tabu_search<NW, TRACE, true, WPS, HALF, PERK>(child, N, a.key, a.inst, gg, max_iter, budget,
+                                                                 Cs, trace, trace_cap, trace_len, lane, link, xseq)
+                 : tabu_search<NW, TRACE, false, WPS, HALF, PERK>(child, N, a.key, a.inst, gg, max_iter, budget,
+                                                                  Cs, trace, trace_cap, trace_len, lane, link, xseq);
     }
     if (to.fault) {  // the pair lost step: stop the replica, report it
         st.status = LABS_RUN_SYNC_LOST;
@@ -304,7 +304,7 @@ __device__ __forceinline__ void replica_store_result(const ReplicaState<NW>& st,
 
 // A whole replica from scratch to its stop condition.  WPS = 2: both warps
 // run it (see replica_generation); the lower half stores the result.
-template <int NW, bool TRACE = false, bool SKEW = false, int WPS = 1, int HALF = 0>
+template <int NW, bool TRACE = false, bool SKEW = false, int WPS = 1, int HALF = 0, bool PERK = false>
 __device__ __forceinline__ void replica_run(const ReplicaCfg& a, uint32_t* pop, int32_t* popE,
                                             int32_t* Cs, int4* trace, int64_t trace_cap,
                                             uint32_t* glf, labs_device_result* out, int lane,
@@ -313,8 +313,8 @@ __device__ __forceinline__ void replica_run(const ReplicaCfg& a, uint32_t* pop, 
     int64_t trace_len = 0;
     replica_init<NW, SKEW>(a, pop, popE, st, lane);
     while (!replica_should_stop<NW>(a, st, glf))
-        replica_generation<NW, TRACE, SKEW, WPS, HALF>(a, st, pop, popE, Cs, trace, trace_cap, trace_len, glf,
-                                                       lane, link, xseq);
+        replica_generation<NW, TRACE, SKEW, WPS, HALF, PERK>(a, st, pop, popE, Cs, trace, trace_cap, trace_len,
+                                                             glf, lane, link, xseq);
     if (HALF == 0) replica_store_result<NW>(st, trace_len, out, lane);
 }
 

@@ -101,8 +101,9 @@ __device__ void serve_slot(const ServeArgs& a, int i, int slot, const labs_insta
             }
             if (over) break;
         }
-        used += replica_generation<NW, false, false, WPS, HALF>(cfg, st, pop, popE, Cs, nullptr, 0, trace_len,
-                                                                nullptr, lane, link, &xseq);
+        // correlations updated per k (PERK): a request's warp mostly runs alone on its sub-partition
+        used += replica_generation<NW, false, false, WPS, HALF, true>(cfg, st, pop, popE, Cs, nullptr, 0,
+                                                                      trace_len, nullptr, lane, link, &xseq);
     }
     if (HALF != 0) return;
     if (finished) {

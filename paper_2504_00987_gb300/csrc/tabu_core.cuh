@@ -332,7 +332,7 @@ __device__ __forceinline__ void pivot_windows(const uint32_t (&B)[NW], const uin
 // ascending j for the tie pick.  Both warps take every decision from the
 // same values, so they run the same steps; `xseq` counts the pair's
 // exchanges.  A bounded wait that runs out ends the search with fault set.
-template <int NW, bool TRACE, bool FIX_FIRST = false, int WPS = 1, int HALF = 0>
+template <int NW, bool TRACE, bool FIX_FIRST = false, int WPS = 1, int HALF = 0, bool PERK = false>
 __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key,
                                const uint32_t inst, const uint32_t g, const int max_iter,
                                const int64_t budget, int32_t* __restrict__ Cs,
@@ -344,9 +344,14 @@ __device__ TabuOut tabu_search(uint32_t (&seq)[NW], const int N, const uint2 key
     constexpr int QB = HALF * (NW / WPS), QE = (HALF + 1) * (NW / WPS);  // this warp's q
     // Correlations after a move are recomputed from the pivot's windows when
     // they are short (fewer ALU-pipe instructions than the per-k update: at
-    // N = 64 the per-k update measured 11 % slower with two warps per SM
-    // sub-partition, 5 % faster for a warp alone) and updated per k otherwise.
-    constexpr bool kRecompute = NW <= 4;
+    // N = 64 the per-k update measured 11-15 % slower with two warps per SM
+    // sub-partition) and updated per k otherwise.  PERK (the batch and
+    // service kernels, whose warps mostly run alone on their sub-partition,
+    // so that a step's dependency chain sets its time) always updates per k:
+    // the update needs only the move's windows, not the flipped pivot, which
+    // measured 13 % less time for the 512-instance uneven batch on GB300 and
+    // 8 % less median service latency.
+    constexpr bool kRecompute = NW <= 4 && !PERK;
     uint32_t B[NW], RL[NW], Bb[NW];
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
