@@ -276,7 +276,10 @@ def run_gpu(args) -> None:
     total_ms, e2e_step_ms = parallel.max_over_ranks(pg, [local_ms, sum(e2e_ms) / len(e2e_ms)], dev)
     lbest = min(res, key=lambda r: (r["E"], r["instance"]))
     best_E, best_inst = parallel.best_over_ranks(pg, lbest["E"], lbest["instance"], dev)
-    extras = None if args.no_extras else c2_extras(args, torch, labs, pg, dev, world, rank, stream)
+    extras = None
+    if not args.no_extras:
+        extras = c2_extras(args, torch, labs, pg, dev, world, rank, stream)
+        extras.update(c34_extras(args, torch, labs, pg, dev, world, rank))
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
@@ -357,6 +360,30 @@ def c2_extras(args, torch, labs, pg, dev, world, rank, stream) -> dict:
                         "target_E": {str(r["N"]): r["target_E"] for r in trows}},
         "tts_p50_s": {str(r["N"]): r["p50_s"] for r in trows},
         "tts_p99_s": {str(r["N"]): r["p99_s"] for r in trows},
+    }
+
+
+def c34_extras(args, torch, labs, pg, dev, world, rank) -> dict:
+    """The batched and the served forms beside the headline, shortened so that
+    the default run stays short: the 512-instance uneven batch (the autotuned
+    graph launch, 10 timed launches, and every instance as its own launch) and
+    the solve service on the first --extras-requests requests of the Poisson
+    stream (the plain one-launch-per-request form on the first tenth)."""
+    b = batch_measure(args, torch, labs, pg, dev, world, rank, steps=10, grid=False)
+    nreq = args.extras_requests
+    sv = serve_measure(args, torch, labs, world, rank, nreq, max(1, nreq // 10))
+    return {
+        "batch_uneven_512": {
+            "workload": "512 instances, N~U{40..127}, K~U{50..200}, 10 N^2 steps, seed 7; one persistent "
+                        "graph launch per batch, mean of 10",
+            "ms_per_batch": b["ms_per_batch"], "flip_evals_per_s": b["flip_evals_per_s"],
+            "mapping": b["mapping"],
+            "plain_one_launch_per_instance": b["plain_one_launch_per_instance"],
+            "speedup_vs_plain": b["speedup_vs_plain"]},
+        "serve_poisson": {
+            "workload": serve_config(args, nreq)["workload"] + " (the first requests of the 20,000-request stream)",
+            **{k: sv[k] for k in ("flip_evals_per_s", "latency_s", "target_misses", "in_flight",
+                                  "admission_held_back", "plain_one_launch_per_request")}},
     }
 
 
@@ -726,11 +753,10 @@ def run_skew_ab(args) -> None:
             "per_N": per_n}), flush=True)
 
 
-def run_batch(args) -> None:
-    """512 uneven instances (N ~ U{40..127}, K ~ U{50..200}, 10 N^2 steps) in one autotuned,
-    graph-captured persistent launch vs one launch per instance."""
-    torch, dev, pg, world, rank = gpu_context(args)
-    import paper_2504_00987_gb300 as labs
+def batch_measure(args, torch, labs, pg, dev, world, rank, steps, grid=True) -> dict:
+    """512 uneven instances (N ~ U{40..127}, K ~ U{50..200}, 10 N^2 steps): the autotuned,
+    graph-captured persistent launch (mean of `steps` timed launches, max over ranks),
+    optionally a grid of other mappings, and the plain form (one launch per instance)."""
     from paper_2504_00987_gb300 import workloads
 
     wl = workloads.uneven_batch(512, seed=7, steps_per_n2=10)
@@ -746,29 +772,26 @@ def run_batch(args) -> None:
     else:
         mapping = labs.autotune(inst)
     tune_s = time.perf_counter() - t0
-    def makespan(m, steps):
+
+    def makespan(m, n):
         with labs.Batch(inst, mapping=m) as b:
             for _ in range(args.warmup):
                 b.launch()
             torch.cuda.synchronize()
-            return statistics.mean(timed_launch(torch, lambda: b.launch(stream), stream)[0] for _ in range(steps))
+            return statistics.mean(timed_launch(torch, lambda: b.launch(stream), stream)[0] for _ in range(n))
 
-    ms = parallel.max_over_ranks(pg, [makespan(mapping, args.steps)], dev)[0]
+    ms = parallel.max_over_ranks(pg, [makespan(mapping, steps)], dev)[0]
     total_flips = parallel.sum_over_ranks(pg, [float(flips)], dev)[0]
+    out = {"ms_per_batch": ms, "flip_evals_per_s": total_flips / (ms / 1e3), "mapping": mapping,
+           "autotune_s": tune_s, "instances": len(wl)}
     if args.batch_mapping:
-        if rank == 0:
-            print(json.dumps({"metric": "flip-evals/s", "value": total_flips / (ms / 1e3), "unit": "flip-evals/s",
-                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                              "higher_is_better": True, "dtype": "int32", "data": "synthetic",
-                              "config": {"workload": "batch_uneven_512 (profiling: fixed mapping)",
-                                         "mapping": mapping}}), flush=True)
-        return
-    # other mappings, for the record: one and two warps per replica
-    grid = []
-    for wps in (1, 2):
-        for wpb, bps in ((wps, 1), (wps, 2), (4, 1), (4, 2)):
-            m = {"warps_per_block": wpb, "blocks_per_sm": bps, "order": 0, "warps_per_seq": wps}
-            grid.append({**m, "ms": parallel.max_over_ranks(pg, [makespan(m, 3)], dev)[0]})
+        return out
+    if grid:  # other mappings, for the record: one and two warps per replica
+        out["mappings_ms"] = []
+        for wps in (1, 2):
+            for wpb, bps in ((wps, 1), (wps, 2), (4, 1), (4, 2)):
+                m = {"warps_per_block": wpb, "blocks_per_sm": bps, "order": 0, "warps_per_seq": wps}
+                out["mappings_ms"].append({**m, "ms": parallel.max_over_ranks(pg, [makespan(m, 3)], dev)[0]})
     # plain form: one launch per instance, round robin over 128 streams (the
     # kernels a GPU runs at once), every instance of the batch
     streams = [torch.cuda.Stream() for _ in range(128)]
@@ -779,33 +802,45 @@ def run_batch(args) -> None:
                         stream=streams[i % len(streams)])
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - t1
-    plain_rate = flips / plain_s
-    if rank == 0:
-        value = total_flips / (ms / 1e3)
-        print(json.dumps({
-            "metric": "flip-evals/s", "value": value, "unit": "flip-evals/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "strong", "dtype": "int32", "data": "synthetic",
-            "config": {"workload": "batch_uneven_512: N~U{40..127}, K~U{50..200}, 10 N^2 steps, seed 7",
-                       "mapping": mapping, "autotune_s": tune_s},
-            "mappings_ms": grid,
-            "plain_one_launch_per_instance": {"flip_evals_per_s": plain_rate, "instances": len(wl),
-                                              "streams": len(streams), "wall_s": plain_s},
-            "speedup_vs_plain": value / plain_rate}), flush=True)
+    out["plain_one_launch_per_instance"] = {"flip_evals_per_s": flips / plain_s, "instances": len(wl),
+                                            "streams": len(streams), "wall_s": plain_s}
+    out["speedup_vs_plain"] = out["flip_evals_per_s"] / (flips / plain_s)
+    return out
 
 
-def run_serve(args) -> None:
+def run_batch(args) -> None:
+    """The uneven batch as its own JSON line (`--workload batch`)."""
+    torch, dev, pg, world, rank = gpu_context(args)
+    import paper_2504_00987_gb300 as labs
+
+    r = batch_measure(args, torch, labs, pg, dev, world, rank, args.steps)
+    if rank != 0:
+        return
+    line = {"metric": "flip-evals/s", "value": r["flip_evals_per_s"], "unit": "flip-evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_batch"],
+            "higher_is_better": True, "dtype": "int32", "data": "synthetic"}
+    if args.batch_mapping:
+        line["config"] = {"workload": "batch_uneven_512 (profiling: fixed mapping)", "mapping": r["mapping"]}
+    else:
+        line.update({"scaling": "strong",
+                     "config": {"workload": "batch_uneven_512: N~U{40..127}, K~U{50..200}, 10 N^2 steps, seed 7",
+                                "mapping": r["mapping"], "autotune_s": r["autotune_s"]},
+                     "mappings_ms": r["mappings_ms"],
+                     "plain_one_launch_per_instance": r["plain_one_launch_per_instance"],
+                     "speedup_vs_plain": r["speedup_vs_plain"]})
+    print(json.dumps(line), flush=True)
+
+
+def serve_measure(args, torch, labs, world, rank, requests, baseline_requests) -> dict:
     """Poisson solve requests (mean 200/s, N ~ U{32..160}, K=100, half with a target E = the
     oracle's ten-second best, half capped at 10^5 steps) through the continuous-batching
-    service, and the same stream as one launch per request on a pool of streams."""
-    torch, dev, pg, world, rank = gpu_context(args)
+    service, and a prefix of the same stream as one launch per request on a pool of streams."""
     import numpy as np
 
-    import paper_2504_00987_gb300 as labs
     from paper_2504_00987_gb300 import workloads
 
     targets = load_targets("serve_n32_160")
-    reqs = workloads.poisson_requests(args.requests, 200.0, seed=11)
+    reqs = workloads.poisson_requests(requests, 200.0, seed=11)
     lo, cnt = parallel.split_range(len(reqs), world, rank)
     reqs = reqs[lo:lo + cnt]
 
@@ -854,7 +889,7 @@ def run_serve(args) -> None:
     # one launch per request on a prefix of the same stream, round robin over as many
     # streams as the service had requests in flight on average (at most 128, the
     # number of kernels a GPU runs concurrently)
-    nb = min(len(reqs), args.baseline_requests)
+    nb = min(len(reqs), baseline_requests)
     mean_in_flight = float(np.mean(in_flight)) if in_flight else 1.0
     n_streams = int(min(128, max(1, round(mean_in_flight))))
     streams = [torch.cuda.Stream() for _ in range(n_streams)]
@@ -879,31 +914,46 @@ def run_serve(args) -> None:
     reqs = saved
     lat_b = np.array([done_b[k][1] for k in range(nb)])
     flips_b = sum(labs.decode_results(outs[k], insts[k].N)[0]["flip_evals"] for k in range(nb))
+    return {
+        "requests": requests, "flip_evals_per_s": served_rate,
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "p50_target_mode": float(np.percentile(lat[tmode], 50)) if tmode.any() else None,
+                      "p99_target_mode": float(np.percentile(lat[tmode], 99)) if tmode.any() else None,
+                      "p50_cap_mode": float(np.percentile(lat[~tmode], 50)) if (~tmode).any() else None,
+                      "p99_cap_mode": float(np.percentile(lat[~tmode], 99)) if (~tmode).any() else None},
+        "target_misses": missed, "wall_s": wall, "gpu_busy_s": st["gpu_seconds"], "quanta": st["quanta"],
+        "in_flight": {"mean": mean_in_flight, "max": int(max(in_flight)) if in_flight else 0},
+        "warps_per_request": args.warps_per_request, "pair_quanta": st["pair_quanta"],
+        "admission_held_back": {"slots": st["deferred_slots"], "shared_memory": st["deferred_smem"],
+                                "arena": st["deferred_hbm"]},
+        "arena_bytes": st["arena_bytes"],
+        "plain_one_launch_per_request": {
+            "requests": nb, "streams": n_streams, "flip_evals_per_s": flips_b / wall_b,
+            "latency_p50_s": float(np.percentile(lat_b, 50)),
+            "latency_p99_s": float(np.percentile(lat_b, 99))},
+    }
+
+
+def serve_config(args, requests) -> dict:
+    return {"workload": f"serve_poisson: {requests} requests at 200/s, N~U{{32..160}}, K=100, "
+                        "half target mode (oracle 10 s best, cap 1e7 steps), half 1e5 steps, seed 11",
+            "slots": args.slots or 4096,
+            "quantum": (f"{args.quantum_us} us of device time per slot" if args.quantum_us
+                        else f"{args.quantum_steps} tabu steps per slot")}
+
+
+def run_serve(args) -> None:
+    """The solve service as its own JSON line (`--workload serve`)."""
+    torch, dev, pg, world, rank = gpu_context(args)
+    import paper_2504_00987_gb300 as labs
+
+    r = serve_measure(args, torch, labs, world, rank, args.requests, args.baseline_requests)
     if rank == 0:
-        print(json.dumps({
-            "metric": "flip-evals/s", "value": served_rate, "unit": "flip-evals/s", "n_gpus": world,
-            "higher_is_better": True, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"serve_poisson: {args.requests} requests at 200/s, N~U{{32..160}}, K=100, "
-                                   "half target mode (oracle 10 s best, cap 1e7 steps), half 1e5 steps, seed 11",
-                       "slots": args.slots or 4096,
-                       "quantum": (f"{args.quantum_us} us of device time per slot" if args.quantum_us
-                                   else f"{args.quantum_steps} tabu steps per slot")},
-            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                          "p50_target_mode": float(np.percentile(lat[tmode], 50)) if tmode.any() else None,
-                          "p99_target_mode": float(np.percentile(lat[tmode], 99)) if tmode.any() else None,
-                          "p50_cap_mode": float(np.percentile(lat[~tmode], 50)) if (~tmode).any() else None,
-                          "p99_cap_mode": float(np.percentile(lat[~tmode], 99)) if (~tmode).any() else None},
-            "target_misses": missed, "wall_s": wall, "gpu_busy_s": st["gpu_seconds"], "quanta": st["quanta"],
-            "in_flight": {"mean": mean_in_flight, "max": int(max(in_flight)) if in_flight else 0},
-            "warps_per_request": args.warps_per_request, "pair_quanta": st["pair_quanta"],
-            "admission_held_back": {"slots": st["deferred_slots"], "shared_memory": st["deferred_smem"],
-                                    "arena": st["deferred_hbm"]},
-            "arena_bytes": st["arena_bytes"],
-            "plain_one_launch_per_request": {
-                "requests": nb, "streams": n_streams, "flip_evals_per_s": flips_b / wall_b,
-                "latency_p50_s": float(np.percentile(lat_b, 50)),
-                "latency_p99_s": float(np.percentile(lat_b, 99))},
-        }), flush=True)
+        line = {"metric": "flip-evals/s", "value": r.pop("flip_evals_per_s"), "unit": "flip-evals/s",
+                "n_gpus": world, "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+                "config": serve_config(args, r.pop("requests"))}
+        line.update(r)
+        print(json.dumps(line), flush=True)
 
 
 def run_skew(args) -> None:
@@ -950,7 +1000,7 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="default line without its N=92..120 sweep and time-to-target keys")
+                    help="default line without its N=92..120 sweep, time-to-target, batch and service keys")
     ap.add_argument("--tts-runs", type=int, default=50, help="default line: time-to-target runs per N")
     ap.add_argument("--replicas", type=int, default=0, help="profiling only: override replicas")
     ap.add_argument("--steps-per-replica", type=int, default=0, help="profiling only: override budget")
@@ -965,6 +1015,8 @@ def main() -> None:
     ap.add_argument("--fit-min-n", type=int, default=30,
                     help="tts: smallest N of the second steps fit (above the one-generation floor)")
     ap.add_argument("--requests", type=int, default=20_000, help="serve: requests")
+    ap.add_argument("--extras-requests", type=int, default=2_000,
+                    help="default line: requests of the shortened service run")
     ap.add_argument("--baseline-requests", type=int, default=400, help="serve: plain-form prefix")
     ap.add_argument("--slots", type=int, default=0, help="serve: resident slots")
     ap.add_argument("--quantum-steps", type=int, default=2000, help="serve: tabu steps per slot per quantum")

@@ -44,6 +44,13 @@ def test_gpu_arm_line():
     assert c["kind"] == "oracle" and c["cores"] >= 1 and c["value"] > 0 and c["sample"]
     assert d["gpu_launches"] == 3
     assert "clocks" in d
+    # the other configurations, measured in the same run
+    assert set(d["tts_p50_s"]) == set(d["tts_p99_s"]) == {str(n) for n in range(92, 121, 4)}
+    b = d["batch_uneven_512"]
+    assert b["ms_per_batch"] > 0 and b["flip_evals_per_s"] > 0 and b["speedup_vs_plain"] > 1
+    s = d["serve_poisson"]
+    assert 0 < s["latency_s"]["p50_cap_mode"] <= s["latency_s"]["p99_cap_mode"]
+    assert s["plain_one_launch_per_request"]["requests"] == 200 and s["flip_evals_per_s"] > 0
 
 
 def test_reference_arm_line():
